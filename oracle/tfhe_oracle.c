@@ -1,0 +1,591 @@
+/*
+ * tfhe_oracle.c -- plain, slow, obviously correct CPU oracle for TFHE gate
+ * bootstrapping and the boolean circuits built on it.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: it is used by tests/, by __graft_entry__.smoke() as the
+ * checker, and by the cpu_baseline / reference leg of bench.py.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes (the paper builds on TFHE, section II-A "Torus FHE"):
+ *   - Torus32: a real number mod 1 stored as a 32-bit word x, value x / 2^32.
+ *     All torus arithmetic is uint32 arithmetic (wraps mod 2^32), which is
+ *     exact.
+ *   - LWE sample (A, B) with B = A.S + e (section II-A).
+ *   - Gate bootstrapping = "bootstrapping" then "key switching", the two
+ *     phases the paper times separately (Table "differentialtime", section
+ *     VI-A; Fig. "gpu_execution" names the BS and KS keys).  Their internals
+ *     are those of the TFHE construction the paper adopts: blind rotation as
+ *     n CMux external products of a TGSW key with a TLWE accumulator, sample
+ *     extraction, then LWE-to-LWE key switching.
+ *   - Boolean circuits: ripple-carry adder (Eq. "addres", Eq. "addcarry",
+ *     sections III-A and V-B-1), naive shift-and-add multiplication (section
+ *     III-B-1) and the matrix-vector product of section IV-D with the
+ *     tree-based accumulation of section V-B-2.
+ *
+ * Every polynomial product here is the schoolbook definition of a product in
+ * Z[X]/(X^N+1) evaluated with uint32 wraparound, i.e. exactly mod 2^32.
+ * No randomness is drawn here: key bits, masks and noise are inputs.
+ *
+ * Parity of the noise statistics against a closed form is pinned in the
+ * tests (measured variance vs. derived variance); every other function is
+ * pinned against an independent computation (Karatsuba products, library
+ * convolutions, exact noiseless identities, truth tables, brute force).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t n;          /* LWE dimension                                  */
+    int32_t N;          /* TLWE ring degree (power of two)                */
+    int32_t l;          /* gadget decomposition levels                    */
+    int32_t bg_bit;     /* log2 of the gadget base Bg                     */
+    int32_t ks_t;       /* key-switch decomposition levels                */
+    int32_t ks_basebit; /* log2 of the key-switch base                    */
+} orc_params;
+
+/* Gate opcodes (the boolean gates the paper evaluates, section II-A). */
+enum { ORC_NAND = 0, ORC_AND = 1, ORC_OR = 2, ORC_XOR = 3, ORC_NOR = 4, ORC_XNOR = 5 };
+
+#define ORC_MU (UINT32_C(1) << 29) /* 1/8 on the torus */
+
+/* ------------------------------------------------------------------ */
+/* Polynomial arithmetic in T_N[X] = T[X]/(X^N + 1)                     */
+/* ------------------------------------------------------------------ */
+
+/* out = a * b in Z[X]/(X^N+1), coefficients mod 2^32.
+ * Definition: the term a_i b_j X^(i+j) lands on X^(i+j) when i+j < N and,
+ * because X^N = -1, on -X^(i+j-N) otherwise.  a is any integer polynomial
+ * (digits, key bits), b a torus polynomial. */
+void orc_negacyclic_mul(int32_t N, const int32_t *a, const uint32_t *b, uint32_t *out)
+{
+    for (int32_t k = 0; k < N; k++)
+        out[k] = 0;
+    for (int32_t i = 0; i < N; i++) {
+        uint32_t ai = (uint32_t)a[i];
+        for (int32_t j = 0; j < N - i; j++)      /* i + j <  N: +X^(i+j)   */
+            out[i + j] += ai * b[j];
+        for (int32_t j = N - i; j < N; j++)      /* i + j >= N: -X^(i+j-N) */
+            out[i + j - N] -= ai * b[j];
+    }
+}
+
+/* out = X^k * p for k in [0, 2N); X^N = -1 so X^(2N) = 1. */
+void orc_mul_by_xk(int32_t N, const uint32_t *p, int32_t k, uint32_t *out)
+{
+    k %= 2 * N;
+    if (k < 0)
+        k += 2 * N;
+    for (int32_t i = 0; i < N; i++) {
+        int32_t e = i + k;               /* exponent of the moved term */
+        uint32_t v = p[i];
+        while (e >= N) {                 /* each wrap multiplies by -1 */
+            e -= N;
+            v = (uint32_t)0 - v;
+        }
+        out[e] = v;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Rounding and gadget decomposition                                    */
+/* ------------------------------------------------------------------ */
+
+/* Round a torus element to the nearest multiple of 1/2^bits (ties up) and
+ * return that multiple as an integer mod 2^bits.  Written as the real-number
+ * definition floor(x * 2^bits / 2^32 + 1/2) in 64-bit integers. */
+static uint32_t orc_round_to_bits(uint32_t x, int32_t bits)
+{
+    uint64_t scaled = (uint64_t)x << bits;            /* x * 2^bits (exact)   */
+    uint64_t r = (scaled + (UINT64_C(1) << 31)) >> 32; /* + 1/2, floor        */
+    return (uint32_t)(r & ((UINT64_C(1) << bits) - 1));
+}
+
+/* Mod switch: abar = round(x * 2N) mod 2N, N a power of two. */
+int32_t orc_modswitch(int32_t N, uint32_t x)
+{
+    int32_t bits = 0;
+    while ((1 << bits) < 2 * N)
+        bits++;
+    return (int32_t)orc_round_to_bits(x, bits);
+}
+
+/* Signed gadget decomposition of one torus element: digits d_0..d_{l-1} in
+ * [-Bg/2, Bg/2) with sum_j d_j / Bg^(j+1) the closest multiple of 1/Bg^l to
+ * x (ties up), modulo 1.  Textbook balanced-digit extraction: round, then
+ * peel base-Bg digits from the least significant end, moving any digit
+ * >= Bg/2 down by Bg with a carry into the next digit (the carry out of the
+ * top digit is a whole torus turn and vanishes). */
+void orc_decompose(int32_t bg_bit, int32_t l, uint32_t x, int32_t *d)
+{
+    int64_t bg = (int64_t)1 << bg_bit;
+    int64_t w = orc_round_to_bits(x, bg_bit * l);   /* integer in [0, Bg^l) */
+    for (int32_t j = l - 1; j >= 0; j--) {
+        int64_t r = w % bg;
+        w /= bg;
+        if (r >= bg / 2) {
+            r -= bg;
+            w += 1;
+        }
+        d[j] = (int32_t)r;
+    }
+}
+
+/* Vector form for tests. */
+void orc_decompose_many(int32_t bg_bit, int32_t l, const uint32_t *x, int64_t count, int32_t *d)
+{
+    for (int64_t i = 0; i < count; i++)
+        orc_decompose(bg_bit, l, x[i], d + i * l);
+}
+
+void orc_modswitch_many(int32_t N, const uint32_t *x, int64_t count, int32_t *out)
+{
+    for (int64_t i = 0; i < count; i++)
+        out[i] = orc_modswitch(N, x[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* LWE / TLWE encryption (client side) -- section II-A                   */
+/* ------------------------------------------------------------------ */
+
+/* ct = (A, B), B = A.S + mu + e.  ct has n + 1 words, B last. */
+void orc_lwe_encrypt(int32_t n, const int32_t *s, const uint32_t *mask, int32_t noise,
+                     uint32_t mu, uint32_t *ct)
+{
+    uint32_t b = mu + (uint32_t)noise;
+    for (int32_t i = 0; i < n; i++) {
+        ct[i] = mask[i];
+        b += mask[i] * (uint32_t)s[i];
+    }
+    ct[n] = b;
+}
+
+/* phase(A, B) = B - A.S (as a torus element). */
+uint32_t orc_lwe_phase(int32_t n, const int32_t *s, const uint32_t *ct)
+{
+    uint32_t ph = ct[n];
+    for (int32_t i = 0; i < n; i++)
+        ph -= ct[i] * (uint32_t)s[i];
+    return ph;
+}
+
+/* Batch forms.  cts is [count][n+1]. */
+void orc_lwe_encrypt_bits(int32_t n, const int32_t *s, int64_t count, const uint32_t *masks,
+                          const int32_t *noise, const uint8_t *bits, uint32_t *cts)
+{
+    for (int64_t g = 0; g < count; g++)
+        orc_lwe_encrypt(n, s, masks + g * n, noise[g],
+                        bits[g] ? ORC_MU : (uint32_t)0 - ORC_MU, cts + g * (n + 1));
+}
+
+void orc_lwe_phase_many(int32_t n, const int32_t *s, int64_t count, int64_t stride,
+                        const uint32_t *cts, uint32_t *phase)
+{
+    for (int64_t g = 0; g < count; g++)
+        phase[g] = orc_lwe_phase(n, s, cts + g * stride);
+}
+
+/* Bootstrapping key: BK[i][r][p][N], i < n, r = c*l + j over the 2l rows of a
+ * TGSW sample (c = 0 mask part, c = 1 body part, j = gadget level), p = 0 for
+ * the TLWE mask polynomial a(X), p = 1 for the body b(X).
+ * Row r is a TLWE encryption of 0 under S(X) -- a(X) = mask, b(X) = a*S + e
+ * -- to which s_i * h_j, h_j = 1/Bg^(j+1), is added on polynomial c
+ * (a TGSW encryption of the constant polynomial s_i). */
+void orc_keygen_bk(const orc_params *P, const int32_t *s, const int32_t *S,
+                   const uint32_t *masks, const int32_t *noise, uint32_t *bk)
+{
+    const int32_t n = P->n, N = P->N, rows = 2 * P->l;
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < n; i++) {
+        for (int32_t r = 0; r < rows; r++) {
+            const uint32_t *a = masks + ((int64_t)i * rows + r) * N;
+            const int32_t *e = noise + ((int64_t)i * rows + r) * N;
+            uint32_t *ra = bk + (((int64_t)i * rows + r) * 2 + 0) * N;
+            uint32_t *rb = bk + (((int64_t)i * rows + r) * 2 + 1) * N;
+            orc_negacyclic_mul(N, S, a, rb);          /* b = S * a         */
+            for (int32_t k = 0; k < N; k++) {
+                rb[k] += (uint32_t)e[k];               /*   + e             */
+                ra[k] = a[k];
+            }
+            int32_t c = r / P->l, j = r % P->l;
+            uint32_t h = (uint32_t)1 << (32 - P->bg_bit * (j + 1));
+            uint32_t *target = (c == 0) ? ra : rb;
+            target[0] += (uint32_t)s[i] * h;           /* + s_i * h_j       */
+        }
+    }
+}
+
+/* Key-switching key: KSK[j][q][d-1][n+1] for j < N, q < t, d in 1..base-1:
+ * an LWE encryption under s of d * S_j / base^(q+1).  Digit 0 would be the
+ * encryption of 0 and is never read, so it is not stored. */
+void orc_keygen_ksk(const orc_params *P, const int32_t *s, const int32_t *S,
+                    const uint32_t *masks, const int32_t *noise, uint32_t *ksk)
+{
+    const int32_t n = P->n, N = P->N, t = P->ks_t, bb = P->ks_basebit;
+    const int32_t nd = (1 << bb) - 1;
+#pragma omp parallel for schedule(static)
+    for (int32_t j = 0; j < N; j++)
+        for (int32_t q = 0; q < t; q++)
+            for (int32_t d = 1; d <= nd; d++) {
+                int64_t row = ((int64_t)j * t + q) * nd + (d - 1);
+                uint32_t msg = (uint32_t)d * (uint32_t)S[j] * ((uint32_t)1 << (32 - bb * (q + 1)));
+                orc_lwe_encrypt(n, s, masks + row * n, noise[row], msg, ksk + row * (n + 1));
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* Gate bootstrapping                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Linear part of a bootstrapped gate under the encoding bit 1 -> +1/8,
+ * bit 0 -> -1/8: c = (0, mu_g) + alpha * (ca + cb).  The sign of the phase of
+ * c is the gate's truth value before the bootstrap re-encrypts it. */
+void orc_gate_combine(int32_t n, int32_t op, const uint32_t *ca, const uint32_t *cb, uint32_t *out)
+{
+    uint32_t mu;
+    int32_t alpha;
+    switch (op) {
+    case ORC_NAND: mu = ORC_MU;                     alpha = -1; break;
+    case ORC_AND:  mu = (uint32_t)0 - ORC_MU;       alpha = 1;  break;
+    case ORC_OR:   mu = ORC_MU;                     alpha = 1;  break;
+    case ORC_XOR:  mu = 2 * ORC_MU;                 alpha = 2;  break;
+    case ORC_NOR:  mu = (uint32_t)0 - ORC_MU;       alpha = -1; break;
+    default:       mu = (uint32_t)0 - 2 * ORC_MU;   alpha = -2; break; /* XNOR */
+    }
+    for (int32_t i = 0; i <= n; i++)
+        out[i] = (uint32_t)alpha * (ca[i] + cb[i]);
+    out[n] += mu;
+}
+
+/* Blind rotation.  abar[0..n-1] are the mod-switched mask words, abar[n] the
+ * mod-switched body.  acc starts as the trivial TLWE sample
+ * (0, X^(-bbar) * v), v = mu * (1 + X + ... + X^(N-1)); then for every i a
+ * CMux with BK_i replaces acc by acc + BK_i [x] (X^(abar_i) * acc - acc),
+ * where [x] is the external product: decompose both polynomials of the TLWE
+ * sample into l signed digit polynomials each and sum digit(r) * BK_i[r].
+ * acc is [2][N]: acc[0] = a(X), acc[1] = b(X). */
+void orc_blind_rotate(const orc_params *P, const uint32_t *bk, const int32_t *abar,
+                      uint32_t mu, uint32_t *acc)
+{
+    const int32_t n = P->n, N = P->N, l = P->l, rows = 2 * l;
+    uint32_t *v = malloc(sizeof(uint32_t) * N);
+    uint32_t *rot = malloc(sizeof(uint32_t) * N);
+    uint32_t *diff = malloc(sizeof(uint32_t) * 2 * N);
+    int32_t *dig = malloc(sizeof(int32_t) * rows * N);
+    int32_t *tmpd = malloc(sizeof(int32_t) * l);
+    uint32_t *prod = malloc(sizeof(uint32_t) * N);
+
+    for (int32_t k = 0; k < N; k++) {
+        v[k] = mu;
+        acc[k] = 0;
+    }
+    orc_mul_by_xk(N, v, 2 * N - abar[n], acc + N);
+
+    for (int32_t i = 0; i < n; i++) {
+        /* diff = X^(abar_i) * acc - acc, both polynomials */
+        for (int32_t c = 0; c < 2; c++) {
+            orc_mul_by_xk(N, acc + c * N, abar[i], rot);
+            for (int32_t k = 0; k < N; k++)
+                diff[c * N + k] = rot[k] - acc[c * N + k];
+        }
+        /* digit polynomials: row r = c*l + j holds digit j of polynomial c */
+        for (int32_t c = 0; c < 2; c++)
+            for (int32_t k = 0; k < N; k++) {
+                orc_decompose(P->bg_bit, l, diff[c * N + k], tmpd);
+                for (int32_t j = 0; j < l; j++)
+                    dig[(c * l + j) * N + k] = tmpd[j];
+            }
+        /* acc += sum_r digit_r * BK_i[r]  (both output polynomials) */
+        for (int32_t p = 0; p < 2; p++)
+            for (int32_t r = 0; r < rows; r++) {
+                const uint32_t *row = bk + (((int64_t)i * rows + r) * 2 + p) * N;
+                orc_negacyclic_mul(N, dig + r * N, row, prod);
+                for (int32_t k = 0; k < N; k++)
+                    acc[p * N + k] += prod[k];
+            }
+    }
+    free(v); free(rot); free(diff); free(dig); free(tmpd); free(prod);
+}
+
+/* Sample extraction of coefficient 0: the TLWE sample (a, b) under S(X) has
+ * phase_0 = b_0 - (a*S)_0 = b_0 - a_0 S_0 + sum_{j>=1} a_(N-j) S_j, so the LWE
+ * sample under the coefficient vector of S is a'_0 = a_0, a'_j = -a_(N-j),
+ * b' = b_0.  out has N + 1 words. */
+void orc_sample_extract(int32_t N, const uint32_t *acc, uint32_t *out)
+{
+    out[0] = acc[0];
+    for (int32_t j = 1; j < N; j++)
+        out[j] = (uint32_t)0 - acc[N - j];
+    out[N] = acc[N];
+}
+
+/* Key switching LWE_N -> LWE_n: round every a'_j to t*basebit bits, write it
+ * in base 2^basebit with digit q of weight 1/base^(q+1), and subtract the
+ * key-switching samples selected by the digits from the trivial (0, b'). */
+void orc_keyswitch(const orc_params *P, const uint32_t *ksk, const uint32_t *in, uint32_t *out)
+{
+    const int32_t n = P->n, N = P->N, t = P->ks_t, bb = P->ks_basebit;
+    const int32_t nd = (1 << bb) - 1;
+    for (int32_t i = 0; i < n; i++)
+        out[i] = 0;
+    out[n] = in[N];
+    for (int32_t j = 0; j < N; j++) {
+        uint32_t w = orc_round_to_bits(in[j], t * bb);
+        for (int32_t q = 0; q < t; q++) {
+            int32_t d = (int32_t)((w >> (bb * (t - 1 - q))) & (uint32_t)nd);
+            if (d == 0)
+                continue;                       /* KSK of digit 0 is zero */
+            const uint32_t *row = ksk + (((int64_t)j * t + q) * nd + (d - 1)) * (n + 1);
+            for (int32_t i = 0; i <= n; i++)
+                out[i] -= row[i];
+        }
+    }
+}
+
+/* Bootstrap of one LWE_n sample with output message +-mu: mod switch, blind
+ * rotate, extract, key switch.  in and out have n + 1 words. */
+void orc_bootstrap(const orc_params *P, const uint32_t *bk, const uint32_t *ksk,
+                   const uint32_t *in, uint32_t mu, uint32_t *out)
+{
+    const int32_t n = P->n, N = P->N;
+    int32_t *abar = malloc(sizeof(int32_t) * (n + 1));
+    uint32_t *acc = malloc(sizeof(uint32_t) * 2 * N);
+    uint32_t *big = malloc(sizeof(uint32_t) * (N + 1));
+    for (int32_t i = 0; i <= n; i++)
+        abar[i] = orc_modswitch(N, in[i]);
+    orc_blind_rotate(P, bk, abar, mu, acc);
+    orc_sample_extract(N, acc, big);
+    orc_keyswitch(P, ksk, big, out);
+    free(abar); free(acc); free(big);
+}
+
+/* One bootstrapped gate. */
+void orc_gate(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t op,
+              const uint32_t *ca, const uint32_t *cb, uint32_t *out)
+{
+    uint32_t *c = malloc(sizeof(uint32_t) * (P->n + 1));
+    orc_gate_combine(P->n, op, ca, cb, c);
+    orc_bootstrap(P, bk, ksk, c, ORC_MU, out);
+    free(c);
+}
+
+/* Independent gates; ca/cb/out are [count][n+1].  Threads over gates. */
+void orc_gates(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int64_t count,
+               const uint8_t *ops, const uint32_t *ca, const uint32_t *cb, uint32_t *out,
+               int32_t nthreads)
+{
+    const int64_t w = P->n + 1;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t g = 0; g < count; g++)
+        orc_gate(P, bk, ksk, ops[g], ca + g * w, cb + g * w, out + g * w);
+}
+
+/* Batch of bootstraps of given LWE_n samples (no gate combine). */
+void orc_bootstrap_many(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int64_t count,
+                        const uint32_t *in, uint32_t mu, uint32_t *out, int32_t nthreads)
+{
+    const int64_t w = P->n + 1;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t g = 0; g < count; g++)
+        orc_bootstrap(P, bk, ksk, in + g * w, mu, out + g * w);
+}
+
+/* Stage-by-stage batch entry points, so each stage can be pinned alone. */
+void orc_blind_rotate_many(const orc_params *P, const uint32_t *bk, int64_t count,
+                           const int32_t *abar, uint32_t mu, uint32_t *acc, int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t g = 0; g < count; g++)
+        orc_blind_rotate(P, bk, abar + g * (P->n + 1), mu, acc + g * 2 * P->N);
+}
+
+void orc_keyswitch_many(const orc_params *P, const uint32_t *ksk, int64_t count,
+                        const uint32_t *in, uint32_t *out)
+{
+    for (int64_t g = 0; g < count; g++)
+        orc_keyswitch(P, ksk, in + g * (P->N + 1), out + g * (P->n + 1));
+}
+
+/* ------------------------------------------------------------------ */
+/* Boolean circuits over encrypted integers (bit 0 = least significant) */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const orc_params *P;
+    const uint32_t *bk, *ksk;
+    int64_t gates;      /* bootstraps performed, for accounting */
+} orc_ev;
+
+static void ev_gate(orc_ev *E, int32_t op, const uint32_t *a, const uint32_t *b, uint32_t *out)
+{
+    orc_gate(E->P, E->bk, E->ksk, op, a, b, out);
+    E->gates++;
+}
+
+/* w-bit ripple-carry addition mod 2^w (sections III-A, V-B-1):
+ *   r_i = a_i XOR b_i XOR c_(i-1)                          (Eq. addres)
+ *   c_i = (a_i AND b_i) OR ((a_i XOR b_i) AND c_(i-1))     (Eq. addcarry)
+ * with no carry into bit 0 (so r_0 = a_0 XOR b_0, c_0 = a_0 AND b_0) and no
+ * carry out of bit w-1 (the sum is truncated to w bits).  A, B, R are
+ * [w][n+1]; R may alias neither input. */
+static void ev_add(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    uint32_t *x = malloc(sizeof(uint32_t) * W);
+    uint32_t *g = malloc(sizeof(uint32_t) * W);
+    uint32_t *t = malloc(sizeof(uint32_t) * W);
+    uint32_t *c = malloc(sizeof(uint32_t) * W);
+    for (int32_t i = 0; i < w; i++) {
+        const uint32_t *ai = A + i * W, *bi = B + i * W;
+        uint32_t *ri = R + i * W;
+        if (i == 0) {
+            ev_gate(E, ORC_XOR, ai, bi, ri);
+            if (w > 1)
+                ev_gate(E, ORC_AND, ai, bi, c);
+            continue;
+        }
+        ev_gate(E, ORC_XOR, ai, bi, x);
+        ev_gate(E, ORC_XOR, x, c, ri);
+        if (i == w - 1)
+            break;                                  /* carry out discarded */
+        ev_gate(E, ORC_AND, ai, bi, g);
+        ev_gate(E, ORC_AND, x, c, t);
+        ev_gate(E, ORC_OR, g, t, c);
+    }
+    free(x); free(g); free(t); free(c);
+}
+
+/* w x w -> w truncated naive multiplication (section III-B-1): partial
+ * product i is A AND b_i shifted left by i; the shifted partial products are
+ * accumulated one after another with ripple-carry adders.  Only bits below w
+ * are formed.  acc starts as partial product 0; partial product i is then
+ * added into bits i..w-1 with a (w-i)-bit adder. */
+static void ev_mul(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    uint32_t *pp = malloc(sizeof(uint32_t) * W * w);
+    uint32_t *sum = malloc(sizeof(uint32_t) * W * w);
+    for (int32_t j = 0; j < w; j++)                 /* partial product 0 */
+        ev_gate(E, ORC_AND, A + j * W, B, R + j * W);
+    for (int32_t i = 1; i < w; i++) {
+        int32_t m = w - i;
+        for (int32_t j = 0; j < m; j++)             /* a_j AND b_i, weight i+j */
+            ev_gate(E, ORC_AND, A + j * W, B + i * W, pp + j * W);
+        ev_add(E, m, R + i * W, pp, sum);
+        memcpy(R + i * W, sum, sizeof(uint32_t) * W * m);
+    }
+    free(pp); free(sum);
+}
+
+/* Matrix-vector product y_r = sum_c M[r][c] * v[c] mod 2^w (section IV-D:
+ * every product independent, each output an accumulation).  The products of
+ * one row are reduced by the tree-based accumulation of section V-B-2: at
+ * every level neighbours (0,1), (2,3), ... are added and an odd last element
+ * moves up unchanged, until one number is left.  M is [rows][cols][w][n+1],
+ * v is [cols][w][n+1], Y is [rows][w][n+1]. */
+static void ev_matvec_row(orc_ev *E, int32_t w, int32_t cols, const uint32_t *Mrow,
+                          const uint32_t *v, uint32_t *Y)
+{
+    const int64_t W = E->P->n + 1, num = W * w;
+    uint32_t *terms = malloc(sizeof(uint32_t) * num * cols);
+    uint32_t *next = malloc(sizeof(uint32_t) * num * cols);
+    for (int32_t c = 0; c < cols; c++)
+        ev_mul(E, w, Mrow + c * num, v + c * num, terms + c * num);
+    int32_t cnt = cols;
+    while (cnt > 1) {
+        int32_t k = 0;
+        for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
+            ev_add(E, w, terms + i * num, terms + (i + 1) * num, next + k * num);
+        if (cnt & 1) {
+            memcpy(next + k * num, terms + (cnt - 1) * num, sizeof(uint32_t) * num);
+            k++;
+        }
+        memcpy(terms, next, sizeof(uint32_t) * num * k);
+        cnt = k;
+    }
+    memcpy(Y, terms, sizeof(uint32_t) * num);
+    free(terms); free(next);
+}
+
+/* Batched circuit entry points: instances are independent and are spread
+ * over threads; each instance is evaluated gate by gate in program order.
+ * Return the number of bootstrapped gates evaluated. */
+int64_t orc_add(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
+{
+    const int64_t num = (int64_t)(P->n + 1) * w;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+#endif
+    for (int64_t b = 0; b < batch; b++) {
+        orc_ev E = {P, bk, ksk, 0};
+        ev_add(&E, w, A + b * num, B + b * num, R + b * num);
+        total += E.gates;
+    }
+    return total;
+}
+
+int64_t orc_mul(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
+{
+    const int64_t num = (int64_t)(P->n + 1) * w;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+#endif
+    for (int64_t b = 0; b < batch; b++) {
+        orc_ev E = {P, bk, ksk, 0};
+        ev_mul(&E, w, A + b * num, B + b * num, R + b * num);
+        total += E.gates;
+    }
+    return total;
+}
+
+int64_t orc_matvec(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                   int32_t rows, int32_t cols, const uint32_t *M, const uint32_t *v, uint32_t *Y,
+                   int32_t nthreads)
+{
+    const int64_t num = (int64_t)(P->n + 1) * w;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+#endif
+    for (int32_t r = 0; r < rows; r++) {
+        orc_ev E = {P, bk, ksk, 0};
+        ev_matvec_row(&E, w, cols, M + (int64_t)r * cols * num, v, Y + r * num);
+        total += E.gates;
+    }
+    return total;
+}
+
+int32_t orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

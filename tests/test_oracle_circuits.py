@@ -1,0 +1,114 @@
+"""Pins for the oracle's circuits: decryption equals the plaintext result
+on every output (add, mul mod 2^w; matrix-vector product mod 2^w), and the
+bootstrapped-gate counts equal the counts of the circuit definitions."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import oparams, toy_params
+from paper_2005_01945_gb300 import synth
+
+
+def _counts():
+    path = os.path.join(os.path.dirname(__file__), "golden", "circuit_gate_counts.txt")
+    out = {}
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if len(f) == 5:
+            out[(f[0], int(f[1]), int(f[2]), int(f[3]))] = int(f[4])
+    return out
+
+
+@pytest.fixture(scope="module")
+def toy(orc):
+    p = toy_params(n=8, N=32)
+    P = oparams(p)
+    kd = synth.key_draws(p, 31)
+    bk = orc.keygen_bk(P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+    ksk = orc.keygen_ksk(P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+    return p, P, kd, bk, ksk
+
+
+def _enc_ints(orc, p, P, kd, xs, w, tag):
+    bits = synth.to_bits(xs, w)
+    cd = synth.ct_draws(p, bits.shape, 77, tag)
+    return orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, bits)
+
+
+def _dec_ints(orc, P, kd, cts):
+    return synth.from_bits(orc.decrypt_bits(P, kd.s, cts))
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_add_exhaustive(orc, toy, w):
+    p, P, kd, bk, ksk = toy
+    a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
+    a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
+    R, g = orc.add(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, f"a{w}"),
+                   _enc_ints(orc, p, P, kd, b, w, f"b{w}"))
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a + b) % (1 << w))
+    key = ("add", w, 0, 0)
+    if key in _counts():
+        assert g == len(a) * _counts()[key]
+
+
+@pytest.mark.parametrize("w", [8, 16, 32])
+def test_add_random_wide(orc, toy, w):
+    p, P, kd, bk, ksk = toy
+    a, b = synth.int_pairs(16, w, 5, f"add{w}")
+    R, g = orc.add(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, "wa"),
+                   _enc_ints(orc, p, P, kd, b, w, "wb"))
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a + b) % (1 << w))
+    assert g == 16 * (5 * w - 6)
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_mul_exhaustive(orc, toy, w):
+    p, P, kd, bk, ksk = toy
+    a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
+    a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
+    R, g = orc.mul(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, f"ma{w}"),
+                   _enc_ints(orc, p, P, kd, b, w, f"mb{w}"))
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a * b) % (1 << w))
+    key = ("mul", w, 0, 0)
+    if key in _counts():
+        assert g == len(a) * _counts()[key]
+
+
+@pytest.mark.parametrize("w", [16, 32])
+def test_mul_gate_counts_and_values(orc, toy, w):
+    p, P, kd, bk, ksk = toy
+    a, b = synth.int_pairs(2, w, 6, f"mul{w}")
+    R, g = orc.mul(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, "xa"),
+                   _enc_ints(orc, p, P, kd, b, w, "xb"))
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a * b) % (1 << w))
+    assert g == 2 * _counts()[("mul", w, 0, 0)]
+
+
+def test_matvec_odd_tree(orc, toy):
+    """3 x 5 matrix (an odd number of terms per row exercises the tree's
+    carried element), 4-bit entries."""
+    p, P, kd, bk, ksk = toy
+    w, rows, cols = 4, 3, 5
+    M = synth.random_uints((rows, cols), w, 8, "M")
+    v = synth.random_uints(cols, w, 8, "v")
+    Y, g = orc.matvec(P, bk, ksk, w, _enc_ints(orc, p, P, kd, M, w, "M"),
+                      _enc_ints(orc, p, P, kd, v, w, "v"))
+    want = (M.astype(np.uint64) * v[None, :]).sum(axis=1) % (1 << w)
+    assert np.array_equal(_dec_ints(orc, P, kd, Y), want)
+    assert g == _counts()[("matvec", w, rows, cols)]
+
+
+def test_count_table_consistent():
+    """The stored counts agree with each other through their recurrences."""
+    c = _counts()
+    add = lambda w: 1 if w == 1 else 5 * w - 6
+    mul = lambda w: w * (w + 1) // 2 + sum(add(m) for m in range(1, w))
+    for (kind, w, r, k), g in c.items():
+        if kind == "add":
+            assert g == add(w)
+        elif kind == "mul":
+            assert g == mul(w)
+        else:
+            assert g == r * (k * mul(w) + (k - 1) * add(w))
