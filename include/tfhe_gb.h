@@ -1,0 +1,175 @@
+/*
+ * tfhe_gb.h -- C ABI of the GB300 (sm_103a) TFHE gate-bootstrapping library.
+ *
+ * The library evaluates TFHE boolean gates with one programmable bootstrap
+ * each (the paper's section II-A and Table "differentialtime": bootstrapping
+ * followed by key switching, with a bootstrapping key and a key-switching
+ * key), and the boolean circuits the paper builds from them: ripple-carry
+ * addition (Eq. "addres", Eq. "addcarry"; sections III-A and V-B-1),
+ * shift-and-add multiplication (section III-B-1) and the matrix-vector
+ * product with tree accumulation (sections IV-D and V-B-2).  Independent
+ * gates of a circuit level run together in one batched launch (the paper's
+ * bit coalescing and compound gates, section V-A).
+ *
+ * Conventions used by every entry point:
+ *   - Torus32: a torus element x/2^32 is stored as one 32-bit word.
+ *   - LWE ciphertext array: int32 [count][TFHE_LWE_STRIDE]; words 0..n-1 are
+ *     the mask a, word n the body b, words n+1..TFHE_LWE_STRIDE-1 are zero on
+ *     output and ignored on input.  Integers are arrays of ciphertexts of
+ *     their bits, least significant bit first: [batch][width][STRIDE].
+ *   - Bit encoding: bit 1 <-> phase +1/8, bit 0 <-> phase -1/8.
+ *   - Ciphertext pointers passed to the evaluation calls are DEVICE pointers
+ *     on the context's device, owned by the caller; outputs must not alias
+ *     inputs.  Key pointers may be host or device memory (detected).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL means the legacy default stream).  Argument errors are
+ *     returned synchronously; errors raised by kernels (bad gather index,
+ *     timeout of a bounded wait) are recorded in a device status word that
+ *     tfhe_ctx_status() reads after the stream has been synchronised.
+ *   - Every function returns a tfhe_status code; tfhe_last_error() gives the
+ *     message of the last failure on that context.
+ *   - A context is used by one host thread at a time (the serving API is the
+ *     multi-request interface).
+ */
+#ifndef TFHE_GB_H
+#define TFHE_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TFHE_GB_ABI_VERSION 1
+#define TFHE_LWE_STRIDE 512   /* words per LWE ciphertext row (n <= 511)   */
+#define TFHE_BIG_STRIDE 1056  /* words per extracted LWE_N row (N + 1 used) */
+
+typedef struct tfhe_ctx tfhe_ctx; /* opaque, owned by the library */
+
+/* Parameter set (section II-A names LWE dimension and key size; the values
+ * are those of TFHE's gate bootstrapping): LWE dimension n, TLWE ring degree
+ * N with k = 1, gadget base 2^bg_bit with l levels, key-switch base
+ * 2^ks_basebit with ks_t levels.  This build supports n <= 511, N = 1024,
+ * k = 1, bg_bit = 10, l = 2, ks_t = 8, ks_basebit = 2; anything else is
+ * rejected with TFHE_EINVAL. */
+typedef struct {
+    int32_t n, N, k, l, bg_bit, ks_t, ks_basebit;
+} tfhe_params;
+
+typedef enum {
+    TFHE_OK = 0,
+    TFHE_EINVAL = -1,   /* bad argument                                  */
+    TFHE_ENOMEM = -2,   /* device allocation failed                      */
+    TFHE_ECUDA = -3,    /* CUDA runtime error                            */
+    TFHE_ETIMEOUT = -4, /* a bounded device or host wait gave up         */
+    TFHE_EBUSY = -5,    /* resource in use (e.g. serving already started) */
+    TFHE_EDEVICE = -6   /* a kernel reported an error in the status word */
+} tfhe_status;
+
+/* Gate opcodes.  Gate g computes c = (0, mu_g) + alpha_g * (ca + cb) and
+ * bootstraps it:  NAND (+1/8, -1), AND (-1/8, +1), OR (+1/8, +1),
+ * XOR (+1/4, +2), NOR (-1/8, -1), XNOR (-1/4, -2). */
+typedef enum {
+    TFHE_NAND = 0, TFHE_AND = 1, TFHE_OR = 2, TFHE_XOR = 3, TFHE_NOR = 4, TFHE_XNOR = 5
+} tfhe_gate;
+
+/* ------------------------------------------------------------------ */
+/* Context and keys                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  Returns TFHE_EINVAL for an
+ * unsupported parameter set.  *out is NULL on failure. */
+int tfhe_ctx_create(const tfhe_params *params, int device, tfhe_ctx **out);
+
+/* Upload keys (host or device pointers; copied, the caller keeps them):
+ *   bk : int32 [n][2l][2][N]  bootstrapping key in coefficient form; row
+ *        r = c*l + j of BK_i is a TLWE sample (a(X), b(X)) of a TGSW
+ *        encryption of s_i (section II-A; Fig. "gpu_execution" "BS key").
+ *        The context keeps it in the NTT domain of its two primes.
+ *   ksk: int32 [N][ks_t][2^ks_basebit - 1][n + 1] key-switching key; entry
+ *        [j][q][d-1] is an LWE_n encryption of d * S_j / base^(q+1)
+ *        (Fig. "gpu_execution" "KS key").
+ * Synchronous with respect to `stream` (returns after the upload). */
+int tfhe_ctx_set_keys(tfhe_ctx *ctx, const int32_t *bk, const int32_t *ksk, void *stream);
+
+void tfhe_ctx_destroy(tfhe_ctx *ctx);
+
+/* Last error message of the context (NUL-terminated, truncated to len). */
+int tfhe_last_error(const tfhe_ctx *ctx, char *buf, size_t len);
+
+/* Read and clear the device status word (synchronises the context's
+ * device).  Returns TFHE_OK or TFHE_EDEVICE; *code (may be NULL) receives
+ * the raw word: bit 0 gather index out of range, bit 1 scatter index out of
+ * range, bit 2 bounded wait timed out. */
+int tfhe_ctx_status(tfhe_ctx *ctx, uint32_t *code);
+
+/* ------------------------------------------------------------------ */
+/* Gate bootstrapping                                                   */
+/* ------------------------------------------------------------------ */
+
+/* count independent bootstrapped gates: out[g] = ops[g](a[g], b[g]).
+ * ops: uint8 [count] device; a, b, out: [count][TFHE_LWE_STRIDE] device.
+ * The batch runs as one blind-rotation launch and one key-switch launch.
+ * count == 0 is a no-op. */
+int tfhe_bootstrap_gates(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int32_t *b,
+                         int32_t *out, size_t count, void *stream);
+
+/* Bootstrap count ciphertexts as they are (no gate combine): the output
+ * encrypts +mu if the input phase lies in [0, 1/2), else -mu. */
+int tfhe_bootstrap(tfhe_ctx *ctx, const int32_t *in, int32_t *out, size_t count, uint32_t mu,
+                   void *stream);
+
+/* Stages of the bootstrap, exposed for testing and profiling:
+ * blind rotation with fused gate combine, mod switch and sample extraction
+ * (ops may be NULL: then b is ignored and a is bootstrapped as is with
+ * mu = 1/8) writing LWE_N samples big: int32 [count][TFHE_BIG_STRIDE]
+ * (a'_0..a'_(N-1), b' at word N); and key switching of those samples. */
+int tfhe_blind_rotate_extract(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a,
+                              const int32_t *b, int32_t *big, size_t count, void *stream);
+int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Circuits over encrypted integers (bit 0 first)                        */
+/* ------------------------------------------------------------------ */
+
+/* R = A + B mod 2^width, batch instances.  A, B, R: [batch][width][STRIDE]. */
+int tfhe_add_n(tfhe_ctx *ctx, int width, const int32_t *A, const int32_t *B, int32_t *R,
+               size_t batch, void *stream);
+
+/* R = A * B mod 2^width (truncated shift-and-add), batch instances. */
+int tfhe_mul_n(tfhe_ctx *ctx, int width, const int32_t *A, const int32_t *B, int32_t *R,
+               size_t batch, void *stream);
+
+/* y = M v mod 2^width: M [rows][cols][width][STRIDE], v [cols][width][STRIDE],
+ * y [rows][width][STRIDE]; products accumulated by a balanced pairwise tree. */
+int tfhe_matvec(tfhe_ctx *ctx, int width, int rows, int cols, const int32_t *M,
+                const int32_t *v, int32_t *y, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Client-side helpers (key generation and encryption on the device)     */
+/* ------------------------------------------------------------------ */
+
+/* Key generation from raw draws (all device pointers):
+ *   s [n], S [N] key bits; bk_mask uint32 [n][2l][N], bk_noise int32
+ *   [n][2l][N]; ksk_mask uint32 [N][ks_t][base-1][n], ksk_noise int32
+ *   [N][ks_t][base-1].  Writes bk_out [n][2l][2][N] and ksk_out
+ *   [N][ks_t][base-1][n+1] in the layouts tfhe_ctx_set_keys takes. */
+int tfhe_keygen(const tfhe_params *params, const int32_t *s, const int32_t *S,
+                const uint32_t *bk_mask, const int32_t *bk_noise, const uint32_t *ksk_mask,
+                const int32_t *ksk_noise, int32_t *bk_out, int32_t *ksk_out, void *stream);
+
+/* Encrypt count bits (device pointers): cts[g] = (mask[g], <mask[g], s> +
+ * (bit ? +1/8 : -1/8) + noise[g]); masks uint32 [count][n]. */
+int tfhe_encrypt_bits(const tfhe_params *params, const int32_t *s, const uint32_t *masks,
+                      const int32_t *noise, const uint8_t *bits, int32_t *cts, size_t count,
+                      void *stream);
+
+/* phase[g] = b - <a, s> (device pointers); decrypt = phase > 0 as int32. */
+int tfhe_phase(const tfhe_params *params, const int32_t *s, const int32_t *cts, uint32_t *phase,
+               size_t count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFHE_GB_H */

@@ -1,0 +1,253 @@
+"""Thin Python binding of libtfhe_gb.so (ctypes; argument marshalling only).
+
+Every computation runs in the library's CUDA kernels.  Device arrays are
+torch CUDA tensors (PyTorch provides device memory and streams); host
+arrays for key upload may be numpy arrays.  If the library has not been
+built this module raises on first use -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .synth import TFHEParams
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtfhe_gb.so")
+
+LWE_STRIDE = 512
+BIG_STRIDE = 1056
+MU = 1 << 29
+NAND, AND, OR, XOR, NOR, XNOR = range(6)
+GATE_NAMES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR"]
+
+_STATUS = {0: "TFHE_OK", -1: "TFHE_EINVAL", -2: "TFHE_ENOMEM", -3: "TFHE_ECUDA",
+           -4: "TFHE_ETIMEOUT", -5: "TFHE_EBUSY", -6: "TFHE_EDEVICE"}
+
+
+class TFHEError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("n", "N", "k", "l", "bg_bit", "ks_t", "ks_basebit")]
+
+    @classmethod
+    def of(cls, p: TFHEParams) -> "CParams":
+        return cls(p.n, p.N, 1, p.l, p.bg_bit, p.ks_t, p.ks_basebit)
+
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "tfhe_ctx_create": (ctypes.c_int, [ctypes.POINTER(CParams), ctypes.c_int, ctypes.c_void_p]),
+    "tfhe_ctx_set_keys": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "tfhe_ctx_destroy": (None, [ctypes.c_void_p]),
+    "tfhe_last_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
+    "tfhe_ctx_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "tfhe_bootstrap_gates": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_bootstrap": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_uint32,
+                                                             ctypes.c_void_p]),
+    "tfhe_blind_rotate_extract": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t,
+                                                                        ctypes.c_void_p]),
+    "tfhe_keyswitch": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_add_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
+                   + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_mul_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
+                   + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                    + [ctypes.c_void_p] * 4),
+    "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 10),
+    "tfhe_encrypt_bits": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 5
+                          + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_phase": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 3
+                   + [ctypes.c_size_t, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libtfhe_gb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(x.ctypes.data)
+    assert x.is_contiguous(), "tensors passed to the library must be contiguous"
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _dev(x, dtype=None):
+    import torch
+    assert isinstance(x, torch.Tensor) and x.is_cuda, "expected a CUDA tensor"
+    if dtype is not None:
+        assert x.dtype == dtype, f"expected {dtype}, got {x.dtype}"
+    assert x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = ""
+        if ctx is not None:
+            buf = ctypes.create_string_buffer(512)
+            lib().tfhe_last_error(ctx, buf, 512)
+            msg = buf.value.decode(errors="replace")
+        raise TFHEError(rc, msg)
+
+
+class Context:
+    """A device context holding the bootstrapping and key-switching keys."""
+
+    def __init__(self, params: TFHEParams | None = None, device: int = 0):
+        self.params = params or TFHEParams()
+        self.cparams = CParams.of(self.params)
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().tfhe_ctx_create(ctypes.byref(self.cparams), device, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tfhe_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(rc, self._h)
+
+    def set_keys(self, bk, ksk, stream=None):
+        """bk int32 [n][4][2][N], ksk int32 [N][t][3][n+1]; host or device."""
+        self._c(lib().tfhe_ctx_set_keys(self._h, _ptr(bk), _ptr(ksk), _stream(stream)))
+
+    def status(self) -> int:
+        code = ctypes.c_uint32(0)
+        rc = lib().tfhe_ctx_status(self._h, ctypes.byref(code))
+        if rc not in (0, -6):
+            self._c(rc)
+        return int(code.value)
+
+    def bootstrap_gates(self, ops, a, b, out, stream=None):
+        import torch
+        count = ops.numel()
+        self._c(lib().tfhe_bootstrap_gates(self._h, _dev(ops, torch.uint8), _dev(a, torch.int32),
+                                           _dev(b, torch.int32), _dev(out, torch.int32), count,
+                                           _stream(stream)))
+
+    def bootstrap(self, x, out, mu=MU, stream=None):
+        import torch
+        count = x.shape[0]
+        self._c(lib().tfhe_bootstrap(self._h, _dev(x, torch.int32), _dev(out, torch.int32), count,
+                                     mu, _stream(stream)))
+
+    def blind_rotate_extract(self, ops, a, b, big, stream=None):
+        import torch
+        count = a.shape[0]
+        self._c(lib().tfhe_blind_rotate_extract(
+            self._h, None if ops is None else _dev(ops, torch.uint8), _dev(a, torch.int32),
+            None if b is None else _dev(b, torch.int32), _dev(big, torch.int32), count,
+            _stream(stream)))
+
+    def keyswitch(self, big, out, stream=None):
+        import torch
+        self._c(lib().tfhe_keyswitch(self._h, _dev(big, torch.int32), _dev(out, torch.int32),
+                                     big.shape[0], _stream(stream)))
+
+    def add_n(self, width, A, B, R, stream=None):
+        import torch
+        batch = A.shape[0]
+        self._c(lib().tfhe_add_n(self._h, width, _dev(A, torch.int32), _dev(B, torch.int32),
+                                 _dev(R, torch.int32), batch, _stream(stream)))
+
+    def mul_n(self, width, A, B, R, stream=None):
+        import torch
+        batch = A.shape[0]
+        self._c(lib().tfhe_mul_n(self._h, width, _dev(A, torch.int32), _dev(B, torch.int32),
+                                 _dev(R, torch.int32), batch, _stream(stream)))
+
+    def matvec(self, width, M, v, y, stream=None):
+        import torch
+        rows, cols = M.shape[0], M.shape[1]
+        self._c(lib().tfhe_matvec(self._h, width, rows, cols, _dev(M, torch.int32),
+                                  _dev(v, torch.int32), _dev(y, torch.int32), _stream(stream)))
+
+
+# ------------------------------------------------------------- client side
+
+def keygen(params: TFHEParams, s, S, bk_mask, bk_noise, ksk_mask, ksk_noise, stream=None):
+    """Device key generation from device draws -> (bk, ksk) int32 tensors."""
+    import torch
+    p = params
+    dev = s.device
+    bk = torch.empty((p.n, 2 * p.l, 2, p.N), dtype=torch.int32, device=dev)
+    ksk = torch.empty((p.N, p.ks_t, p.ks_digits, p.n + 1), dtype=torch.int32, device=dev)
+    cp = CParams.of(p)
+    _check(lib().tfhe_keygen(ctypes.byref(cp), _dev(s), _dev(S), _dev(bk_mask), _dev(bk_noise),
+                             _dev(ksk_mask), _dev(ksk_noise), _dev(bk), _dev(ksk),
+                             _stream(stream)))
+    return bk, ksk
+
+
+def encrypt_bits(params: TFHEParams, s, masks, noise, bits, stream=None):
+    """bits uint8 [...]; masks uint32-as-int32 [..., n]; -> int32 [..., 512]."""
+    import torch
+    out = torch.empty(tuple(bits.shape) + (LWE_STRIDE,), dtype=torch.int32, device=bits.device)
+    cp = CParams.of(params)
+    _check(lib().tfhe_encrypt_bits(ctypes.byref(cp), _dev(s), _dev(masks), _dev(noise),
+                                   _dev(bits, torch.uint8), _dev(out), bits.numel(),
+                                   _stream(stream)))
+    return out
+
+
+def phase(params: TFHEParams, s, cts, stream=None):
+    """-> int32 tensor of phases (b - <a, s>) with the leading shape of cts."""
+    import torch
+    count = cts.numel() // LWE_STRIDE
+    out = torch.empty(cts.shape[:-1], dtype=torch.int32, device=cts.device)
+    cp = CParams.of(params)
+    _check(lib().tfhe_phase(ctypes.byref(cp), _dev(s), _dev(cts), _dev(out), count,
+                            _stream(stream)))
+    return out
+
+
+def decrypt_bits(params: TFHEParams, s, cts, stream=None):
+    return (phase(params, s, cts, stream) > 0).to(dtype=__import__("torch").uint8)
+
+
+def to_device(a: np.ndarray, device="cuda"):
+    """numpy (u)int32/uint8 array -> torch tensor on device (uint32 viewed as int32)."""
+    import torch
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device)

@@ -1,0 +1,73 @@
+// common.cuh -- shared definitions of the sm_103a TFHE kernels.
+//
+// Ring and gadget shape are compile-time: N = 1024, k = 1, l = 2,
+// Bg = 2^10, key switch t = 8, base 4.  The LWE dimension n is a runtime
+// value (n <= 511).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tfhe_gb.h"
+
+namespace tgb {
+
+constexpr int kN = 1024;                 // TLWE ring degree
+constexpr int kL = 2;                    // gadget levels
+constexpr int kRows = 2 * kL;            // rows of a TGSW sample (k = 1)
+constexpr int kBgBit = 10;               // log2 Bg
+constexpr int kKsT = 8;                  // key-switch levels
+constexpr int kKsBaseBit = 2;            // log2 key-switch base
+constexpr int kKsDigits = (1 << kKsBaseBit) - 1;
+constexpr int kLweStride = TFHE_LWE_STRIDE;
+constexpr int kBigStride = TFHE_BIG_STRIDE;
+constexpr int kMaxN = kLweStride - 1;
+constexpr uint32_t kMu = 1u << 29;       // 1/8
+
+// Word offset that turns signed gadget digits into unsigned bit fields:
+// 1/2 Bg per level plus the rounding half of the last level.
+constexpr uint32_t kDecompOffset = (1u << 31) + (1u << 21) + (1u << 11);
+
+// Two NTT primes below 2^28 with 2048 | q - 1.  Their product P ~ 2^56
+// exceeds twice the largest magnitude of an exact external-product
+// coefficient, 4 * N * 2^9 * 2^31 = 2^52, so the centred CRT lift is the
+// exact integer.  q < 2^28 keeps every lazy value below 2^32 and the 4-term
+// pointwise sum of [0,4q) x [0,q) products below q * 2^32.
+constexpr uint32_t kQ0 = 268369921u;     // 0x0FFF0001
+constexpr uint32_t kQ1 = 268367873u;     // 0x0FFEF801
+
+// Status word bits (device-side errors).
+constexpr uint32_t kErrGather = 1u;
+constexpr uint32_t kErrScatter = 2u;
+constexpr uint32_t kErrTimeout = 4u;
+
+// x * w mod q in [0, 2q) for any 32-bit x, with wp = floor(w 2^32 / q)
+// (Shoup's precomputed-quotient multiplication).
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t wp, uint32_t q)
+{
+    return x * w - __umulhi(x, wp) * q;
+}
+
+// x in [0, 2m) -> [0, m): subtract m when x >= m (unsigned min trick).
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m)
+{
+    return min(x, x - m);
+}
+
+// Montgomery reduction of a 64-bit x < q 2^32: returns x 2^-32 mod q in
+// [0, 2q).  qneg_inv = -q^-1 mod 2^32.
+__device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t qneg_inv)
+{
+    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    uint32_t m = lo * qneg_inv;
+    return hi + __umulhi(m, q) + (lo != 0u ? 1u : 0u);
+}
+
+// Per-context device pointers and sizes shared by the kernels.
+struct DevKeys {
+    const uint4 *bk_ntt;   // [n][2 poly][2 prime][32 reg][32 lane] x uint4(4 rows)
+    const uint4 *ksk;      // [N][t][base-1][kLweStride/4] words
+    const uint2 *twb;      // stage-B twiddles [2 prime][2 dir][32 reg][32 lane] (w, w')
+    int n;
+};
+
+}  // namespace tgb

@@ -1,0 +1,63 @@
+// runtime.h -- host-side context shared by the C-ABI translation units.
+#pragma once
+#include <string>
+
+#include "common.cuh"
+
+struct tfhe_ctx {
+    int device = 0;
+    tfhe_params prm{};
+    int num_sms = 0;
+    int br_grid = 0;                 // persistent blind-rotation grid
+    uint2 *twb = nullptr;            // stage-B twiddles
+    uint32_t *bk_ntt = nullptr;      // bootstrapping key, NTT domain
+    uint4 *ksk = nullptr;            // key-switching key, padded rows
+    uint32_t *status = nullptr;      // device status word
+    int32_t *big = nullptr;          // LWE_N scratch between the two stages
+    size_t big_rows = 0;
+    bool keys_loaded = false;
+    tgb::DevKeys keys{};
+    std::string err;
+    struct CircuitCache *circuits = nullptr;
+    struct Server *server = nullptr;
+};
+
+namespace tgb {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+int fail(tfhe_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(tfhe_ctx *ctx, cudaError_t e, const char *where);
+bool params_supported(const tfhe_params *p);
+int ensure_big(tfhe_ctx *ctx, size_t rows);
+int run_bootstrap(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int32_t *idx_a,
+                  long rows_a, const int32_t *b, const int32_t *idx_b, long rows_b, int32_t *out,
+                  const int32_t *idx_out, long rows_out, long count, uint32_t mu,
+                  cudaStream_t stream);
+
+cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const int32_t *in_a,
+                                const int32_t *idx_a, long rows_a, const int32_t *in_b,
+                                const int32_t *idx_b, long rows_b, int32_t *big, long count,
+                                uint32_t mu, uint32_t *status, int grid, cudaStream_t stream);
+cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
+                             const int32_t *idx_out, long rows_out, long count, int n,
+                             int num_sms, uint32_t *status, cudaStream_t stream);
+
+void release_circuits(tfhe_ctx *ctx);
+void release_serving(tfhe_ctx *ctx);
+
+}  // namespace tgb

@@ -1,0 +1,179 @@
+"""GPU parity of gate bootstrapping through the C ABI, bit-exact against the
+oracle: client key generation and encryption, the blind-rotation +
+extraction stage, the key-switch stage, and whole gates."""
+import numpy as np
+import pytest
+
+from conftest import center, oparams, trivial_rotation
+from paper_2005_01945_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+M32 = 1 << 32
+MU = 1 << 29
+
+
+@pytest.fixture(scope="module")
+def gpu(orc):
+    import torch
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    p = synth.TFHEParams()
+    P = oparams(p)
+    kd = synth.key_draws(p, synth.MASTER_SEED)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    obk = orc.keygen_bk(P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+    oksk = orc.keygen_ksk(P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+    torch.cuda.synchronize()
+    yield dict(torch=torch, api=api, p=p, P=P, kd=kd, ctx=ctx, bk=bk, ksk=ksk, obk=obk,
+               oksk=oksk, s_dev=d(kd.s))
+    ctx.close()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_keygen_bit_exact(gpu):
+    assert np.array_equal(_u32(gpu["bk"]), gpu["obk"])
+    assert np.array_equal(_u32(gpu["ksk"]), gpu["oksk"])
+
+
+def test_encrypt_and_phase_bit_exact(gpu, orc):
+    api, p, P, kd = gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    bits = synth.random_bits(777, 3, "enc")
+    cd = synth.ct_draws(p, 777, 3, "enc")
+    ct = api.encrypt_bits(p, gpu["s_dev"], api.to_device(cd.mask), api.to_device(cd.noise),
+                          api.to_device(bits))
+    oct_ = orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, bits)
+    got = _u32(ct)
+    assert np.array_equal(got[:, :p.n + 1], oct_)
+    assert not got[:, p.n + 1:].any()
+    ph = _u32(api.phase(p, gpu["s_dev"], ct))
+    assert np.array_equal(ph, orc.phase(P, kd.s, oct_))
+
+
+def _fresh(gpu, orc, count, seed, tag, zero_some=False):
+    """count ciphertext pairs: device tensors and oracle arrays of the same draws."""
+    api, p, P, kd = gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    bits = synth.random_bits((2, count), seed, tag)
+    cd = synth.ct_draws(p, (2, count), seed, tag)
+    if zero_some:   # mask words that mod-switch to 0 exercise the skipped CMux
+        cd.mask[:, :, ::7] = 0
+    cts = orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, bits)
+    dev = api.encrypt_bits(p, gpu["s_dev"], api.to_device(cd.mask), api.to_device(cd.noise),
+                           api.to_device(bits))
+    return bits, cts, dev
+
+
+@pytest.mark.parametrize("count", [1, 8, 37])
+def test_gates_bit_exact(gpu, orc, count):
+    torch, api, p, P, kd = gpu["torch"], gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    bits, cts, dev = _fresh(gpu, orc, count, 10 + count, f"g{count}", zero_some=count == 37)
+    ops = (np.arange(count) % 6).astype(np.uint8)
+    out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
+    got = _u32(out)
+    assert np.array_equal(got[:, :p.n + 1], want)
+    assert not got[:, p.n + 1:].any()
+    assert gpu["ctx"].status() == 0
+
+
+def test_config0_gates8(gpu, orc):
+    """Config 0: NAND, NAND, AND, AND, OR, OR, XOR, XOR on 16 fresh encryptions."""
+    torch, api, p, P, kd = gpu["torch"], gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    ops, ba, bb = synth.gates8_inputs(synth.MASTER_SEED)
+    cd = synth.ct_draws(p, (2, 8), synth.MASTER_SEED, "gates8")
+    ca = orc.encrypt_bits(P, kd.s, cd.mask[0], cd.noise[0], ba)
+    cb = orc.encrypt_bits(P, kd.s, cd.mask[1], cd.noise[1], bb)
+    da = api.encrypt_bits(p, gpu["s_dev"], api.to_device(cd.mask[0]), api.to_device(cd.noise[0]),
+                          api.to_device(ba))
+    db = api.encrypt_bits(p, gpu["s_dev"], api.to_device(cd.mask[1]), api.to_device(cd.noise[1]),
+                          api.to_device(bb))
+    out = torch.empty((8, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), da, db, out)
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, ca, cb)
+    assert np.array_equal(_u32(out)[:, :p.n + 1], want)
+    truth = {0: lambda a, b: 1 - (a & b), 1: lambda a, b: a & b, 2: lambda a, b: a | b,
+             3: lambda a, b: a ^ b}
+    dec = orc.decrypt_bits(P, kd.s, want)
+    assert all(dec[k] == truth[int(ops[k])](int(ba[k]), int(bb[k])) for k in range(8))
+
+
+def test_blind_rotate_extract_stage(gpu, orc):
+    torch, api, p, P, kd = gpu["torch"], gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    count = 6
+    bits, cts, dev = _fresh(gpu, orc, count, 20, "br", zero_some=True)
+    big = torch.zeros((count, 1056), dtype=torch.int32, device="cuda")
+    gpu["ctx"].blind_rotate_extract(None, dev[0], None, big)
+    abar = orc.modswitch(cts[0].reshape(-1), p.N).reshape(count, p.n + 1)
+    acc = orc.blind_rotate(P, gpu["obk"], abar)
+    want = np.stack([orc.sample_extract(P, acc[g]) for g in range(count)])
+    assert np.array_equal(_u32(big)[:, :p.N + 1], want)
+
+
+@pytest.mark.parametrize("count", [3, 5000])
+def test_keyswitch_stage(gpu, orc, count):
+    """Small batches take the split-j atomic path, large ones the direct one."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    rng = np.random.default_rng(count)
+    big = rng.integers(0, M32, size=(count, 1056), dtype=np.uint64).astype(np.uint32)
+    out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].keyswitch(api.to_device(big), out)
+    sample = np.arange(count) if count < 100 else rng.choice(count, 64, replace=False)
+    want = orc.keyswitch(P, gpu["oksk"], np.ascontiguousarray(big[sample, :p.N + 1]))
+    got = _u32(out)[sample]
+    assert np.array_equal(got[:, :p.n + 1], want)
+    assert not got[:, p.n + 1:].any()
+
+
+def test_trivial_keys_exact_rotation_large_batch(orc):
+    """Zero-mask, zero-noise bootstrapping key: after blind rotation the
+    extracted sample is exactly (0, coefficient 0 of X^m v) for every gate of
+    a batch larger than the persistent grid."""
+    import torch
+    from paper_2005_01945_gb300 import api
+    p = synth.TFHEParams()
+    kd = synth.key_draws(p, 99, noiseless=True, zero_bk_mask=True)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    count = 3001
+    rng = np.random.default_rng(5)
+    ct = rng.integers(0, M32, size=(count, 512), dtype=np.uint64).astype(np.uint32)
+    ct[:, p.n + 1:] = 0
+    big = torch.zeros((count, 1056), dtype=torch.int32, device="cuda")
+    ctx.blind_rotate_extract(None, d(ct), None, big)
+    got = _u32(big)
+    abar = orc.modswitch(ct[:, :p.n + 1].reshape(-1), p.N).reshape(count, p.n + 1).astype(np.int64)
+    m = ((abar[:, :p.n] * kd.s).sum(axis=1) - abar[:, p.n]) % (2 * p.N)
+    coef0 = np.array([trivial_rotation(MU, p.N, int(mm))[0] for mm in m], dtype=np.uint32)
+    assert not got[:, :p.N].any()
+    assert np.array_equal(got[:, p.N], coef0)
+    ctx.close()
+
+
+def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
+    """A batch of 2000 gates (several persistent-grid rounds): every output
+    decrypts to the gate's truth value; 12 sampled outputs are bit-exact."""
+    torch, api, p, P, kd = gpu["torch"], gpu["api"], gpu["p"], gpu["P"], gpu["kd"]
+    count = 2000
+    bits, cts, dev = _fresh(gpu, orc, count, 30, "many")
+    ops = synth._gen(30, "ops").integers(0, 6, size=count).astype(np.uint8)
+    out = torch.empty((count, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+    got = _u32(out)
+    a, b = bits[0].astype(int), bits[1].astype(int)
+    truth = np.select([ops == 0, ops == 1, ops == 2, ops == 3, ops == 4, ops == 5],
+                      [1 - (a & b), a & b, a | b, a ^ b, 1 - (a | b), 1 - (a ^ b)])
+    dec = orc.decrypt_bits(P, kd.s, got[:, :p.n + 1])
+    assert np.array_equal(dec, truth.astype(np.uint8))
+    sample = synth._gen(31, "sample").choice(count, 12, replace=False)
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops[sample], cts[0][sample], cts[1][sample])
+    assert np.array_equal(got[sample, :p.n + 1], want)
