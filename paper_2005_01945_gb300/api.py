@@ -60,7 +60,7 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
     "tfhe_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
                     + [ctypes.c_void_p] * 4),
-    "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 10),
+    "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 9),
     "tfhe_encrypt_bits": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 5
                           + [ctypes.c_size_t, ctypes.c_void_p]),
     "tfhe_phase": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 3

@@ -37,3 +37,20 @@ def test_invalid_params_rejected_without_gpu():
     h = ctypes.c_void_p()
     assert L.tfhe_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == -1
     assert not h.value
+
+
+def declared_arity():
+    src = open(os.path.join(ROOT, "include", "tfhe_gb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, args in re.findall(r"\b(tfhe_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+        args = args.strip()
+        out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header():
+    from paper_2005_01945_gb300 import api
+    arity = declared_arity()
+    for name, (_, argtypes) in api.EXPORTS.items():
+        assert len(argtypes) == arity[name], (name, len(argtypes), arity[name])
