@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark: bootstrapped gates per second on one GB300.
+
+Workload (one step): a batch of 256 homomorphic 32-bit ripple-carry
+additions of uniform random operands encrypted bitwise with TFHE (LWE
+n=500, TLWE N=1024, Bg=2^10, l=2, key switch t=8, base 4): 154 bootstrapped
+gates each, 39,424 per step, scheduled as 62 levels of batched bootstraps
+replayed as one CUDA graph.  Also reported: single-request 32-bit
+multiplication latency (p50/p99), level-batched versus one launch pair per
+gate, and the CPU oracle's gate rate on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas, no collective on the data path); value counts all ranks' gates
+over the slowest rank's time.  ``--impl reference`` times the CPU oracle
+(rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "bootstrapped gates/sec on 1 GB300; 32-bit enc. mul p50/p99 latency, batched vs per-gate"
+WORKLOAD = ("256 homomorphic 32-bit ripple-carry additions per step (39,424 bootstrapped gates, "
+            "62 levels); TFHE LWE n=500, TLWE N=1024 k=1, Bg=2^10 l=2, key switch t=8 base 4, "
+            "Torus32; keys, noise and operands from one seed")
+BATCH, WIDTH = 256, 32
+GATES_PER_ADD = 5 * WIDTH - 6
+
+# Algorithmic 32-bit integer operations of one CMux step of the NTT-based
+# external product (derivation in DESIGN.md, "Roofline"): 12 transforms of
+# 5120 radix-2 butterflies at 7 ops, 12 x 1024 twiddle products at 3 ops,
+# 2 x 2 x 1024 pointwise 4-term products at 12 ops, 4 x 1024 digit
+# extractions at 8 ops, 2 x 1024 CRT lifts + accumulates at 12 ops.
+OPS_PER_CMUX = 12 * 5120 * 7 + 12 * 1024 * 3 + 4 * 1024 * 12 + 4 * 1024 * 8 + 2 * 1024 * 12
+INT32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--latency-samples", type=int, default=6)
+    ap.add_argument("--per-gate-samples", type=int, default=2)
+    ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--cpu-gates", type=int, default=128)
+    ap.add_argument("--br-only", type=int, default=0, help="profile mode: blind rotation alone")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen([exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                      "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                     stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+class OracleSample:
+    """CPU oracle (plain C, OpenMP over gates) on a bounded sample of the
+    workload: the first-level gates (XOR / AND of fresh input bits) of the
+    first additions of the batch, each a full bootstrap + key switch."""
+
+    def __init__(self, ngates, seed):
+        import oracle
+        from paper_2005_01945_gb300 import synth
+        self.oracle = oracle
+        p = synth.TFHEParams()
+        self.P = P = oracle.Params(p.n, p.N, p.l, p.bg_bit, p.ks_t, p.ks_basebit)
+        kd = synth.key_draws(p, seed)
+        self.bk = oracle.keygen_bk(P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+        self.ksk = oracle.keygen_ksk(P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+        a, b = synth.int_pairs(BATCH, WIDTH, seed + 1, "add32")
+        ba, bb = synth.to_bits(a, WIDTH), synth.to_bits(b, WIDTH)
+        cda = synth.ct_draws(p, ba.shape, seed + 1, "add32a")
+        cdb = synth.ct_draws(p, bb.shape, seed + 1, "add32b")
+        k = np.arange(ngates)
+        inst, bit = k // (2 * WIDTH), (k // 2) % WIDTH
+        self.op = np.where(k % 2 == 0, 3, 1).astype(np.uint8)
+        self.ca = oracle.encrypt_bits(P, kd.s, cda.mask[inst, bit], cda.noise[inst, bit],
+                                      ba[inst, bit])
+        self.cb = oracle.encrypt_bits(P, kd.s, cdb.mask[inst, bit], cdb.noise[inst, bit],
+                                      bb[inst, bit])
+        self.ngates = ngates
+        self.cores = oracle.max_threads()
+        self.desc = (f"{ngates} first-level XOR/AND gates of the 32-bit additions of the batch "
+                     f"(full bootstrap + key switch each), OpenMP over gates")
+
+    def rate(self):
+        t0 = time.perf_counter()
+        self.oracle.gates(self.P, self.bk, self.ksk, self.op, self.ca, self.cb,
+                          nthreads=self.cores)
+        return self.ngates / (time.perf_counter() - t0)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2005_01945_gb300 import synth
+    sample = OracleSample(max(16, args.cpu_gates // 4), synth.MASTER_SEED)
+    for _ in range(args.warmup):
+        sample.rate()
+    rates = [sample.rate() for _ in range(args.steps)]
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sample.ngates / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample.desc},
+            "cpu_baseline": {"value": value, "unit": "gates/s", "cores": sample.cores,
+                             "kind": "oracle", "sample": sample.desc},
+            "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_br_only(count):
+    """Blind rotation + extraction alone on `count` fresh gates (profiling)."""
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    kd = synth.key_draws(p, synth.MASTER_SEED)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    bits = synth.random_bits((2, count), 7, "bronly")
+    cd = synth.ct_draws(p, (2, count), 7, "bronly")
+    s_dev = d(kd.s)
+    ca = api.encrypt_bits(p, s_dev, d(cd.mask[0]), d(cd.noise[0]), d(bits[0]))
+    cb = api.encrypt_bits(p, s_dev, d(cd.mask[1]), d(cd.noise[1]), d(bits[1]))
+    ops = d(np.full(count, 3, np.uint8))
+    big = torch.empty((count, api.BIG_STRIDE), dtype=torch.int32, device="cuda")
+    out = torch.empty((count, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    br, ks = [], []
+    for _ in range(3):
+        e0.record()
+        ctx.blind_rotate_extract(ops, ca, cb, big)
+        e1.record()
+        ctx.keyswitch(big, out)
+        e2.record()
+        torch.cuda.synchronize()
+        br.append(e0.elapsed_time(e1))
+        ks.append(e1.elapsed_time(e2))
+    print(json.dumps({"br_only": count, "br_ms": br, "ks_ms": ks,
+                      "bootstraps_per_s": count / (min(br) / 1e3)}), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.br_only:
+        run_br_only(args.br_only)
+        return
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    dev = torch.device("cuda", local)
+
+    # ---- keys and inputs (synthetic, seeded; every rank its own replica)
+    seed = synth.MASTER_SEED + 1000 * rank
+    p = synth.TFHEParams()
+    kd = synth.key_draws(p, seed)
+    d = lambda a: api.to_device(a, dev)  # noqa: E731
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p, device=local)
+    ctx.set_keys(bk, ksk)
+    del bk, ksk
+    s_dev = d(kd.s)
+    a, b = synth.int_pairs(BATCH, WIDTH, seed + 1, "add32")
+    ba, bb = synth.to_bits(a, WIDTH), synth.to_bits(b, WIDTH)
+    cda = synth.ct_draws(p, ba.shape, seed + 1, "add32a")
+    cdb = synth.ct_draws(p, bb.shape, seed + 1, "add32b")
+    A = api.encrypt_bits(p, s_dev, d(cda.mask), d(cda.noise), d(ba))
+    B = api.encrypt_bits(p, s_dev, d(cdb.mask), d(cdb.noise), d(bb))
+    R = torch.empty_like(A)
+    gates_step = BATCH * GATES_PER_ADD
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ctx.set_option(api.OPT_PROFILE, 1)
+    for _ in range(args.warmup):
+        ctx.add_n(WIDTH, A, B, R)
+    torch.cuda.synchronize()
+    ctx.profile()
+
+    # ---- timed region: K steps, L2 flushed between steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, br_ms, br_launch, br_boot, ks_ms = [], 0.0, 0, 0, 0.0
+    launches0 = ctx.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record()
+        ctx.add_n(WIDTH, A, B, R)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pr = ctx.profile()
+        br_ms += pr["br_ms"]
+        br_launch += pr["br_launches"]
+        br_boot += pr["br_bootstraps"]
+        ks_ms += pr["ks_ms"]
+    barrier()
+    launches = ctx.launches() - launches0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = gates_step * args.steps * world / (total_ms / 1e3)
+
+    # ---- correctness of the timed result (decryption on the device)
+    dec = api.decrypt_bits(p, s_dev, R).cpu().numpy()
+    verified = bool(np.array_equal(synth.from_bits(dec), (a + b) % (1 << WIDTH)))
+
+    # ---- end to end: pinned host ciphertexts in, results out, every step
+    ctx.set_option(api.OPT_PROFILE, 0)
+    A_h = A.cpu().pin_memory()
+    B_h = B.cpu().pin_memory()
+    R_h = torch.empty(R.shape, dtype=R.dtype).pin_memory()
+    ctx.add_n(WIDTH, A, B, R)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record()
+        A.copy_(A_h, non_blocking=True)
+        B.copy_(B_h, non_blocking=True)
+        ctx.add_n(WIDTH, A, B, R)
+        R_h.copy_(R, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": gates_step * args.steps * world / (e2e_total / 1e3), "unit": "gates/s",
+           "h2d_bytes_per_step": A.numel() * 4 + B.numel() * 4,
+           "d2h_bytes_per_step": R.numel() * 4}
+
+    # ---- roofline of the dominant kernel (blind rotation), from the events
+    # recorded around its launches inside the timed graph replays
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6
+    ops = OPS_PER_CMUX * p.n * br_boot
+    achieved = ops / (br_ms / 1e3) if br_ms > 0 else 0.0
+    roofline = {"kernel": "k_blind_rotate", "bound": "alu", "achieved": achieved / 1e12,
+                "peak": peak_ops / 1e12, "unit": "Tops/s (int32)", "frac": achieved / peak_ops,
+                "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} INT32 "
+                              f"lanes x {sm_max:.0f} MHz (max SM clock)",
+                "traffic": None, "launches": br_launch, "avg_launch_ms": br_ms / max(br_launch, 1),
+                "share_of_step": br_ms / max(sum(step_ms), 1e-9),
+                "keyswitch_share_of_step": ks_ms / max(sum(step_ms), 1e-9)}
+
+    # ---- 32-bit multiplication latency: level-batched vs one launch pair per gate
+    latency = None
+    if not args.no_latency and rank == 0:
+        ma, mb = synth.int_pairs(1, 32, seed + 2, "lat")
+        da = api.encrypt_bits(p, s_dev, d(synth.ct_draws(p, (1, 32), seed + 2, "la").mask),
+                              d(synth.ct_draws(p, (1, 32), seed + 2, "la").noise),
+                              d(synth.to_bits(ma, 32)))
+        db = api.encrypt_bits(p, s_dev, d(synth.ct_draws(p, (1, 32), seed + 2, "lb").mask),
+                              d(synth.ct_draws(p, (1, 32), seed + 2, "lb").noise),
+                              d(synth.to_bits(mb, 32)))
+        out = torch.empty((1, 32, api.LWE_STRIDE), dtype=torch.int32, device=dev)
+
+        def timed(nsamp):
+            res = []
+            ctx.mul_n(32, da, db, out)
+            torch.cuda.synchronize()
+            for _ in range(nsamp):
+                e0.record()
+                ctx.mul_n(32, da, db, out)
+                e1.record()
+                torch.cuda.synchronize()
+                res.append(e0.elapsed_time(e1))
+            return res
+
+        batched = timed(args.latency_samples)
+        ok_b = bool(synth.from_bits(api.decrypt_bits(p, s_dev, out).cpu().numpy())[0]
+                    == (int(ma[0]) * int(mb[0])) % (1 << 32))
+        ctx.set_option(api.OPT_PER_GATE, 1)
+        per_gate = timed(args.per_gate_samples)
+        ctx.set_option(api.OPT_PER_GATE, 0)
+        ok_p = bool(synth.from_bits(api.decrypt_bits(p, s_dev, out).cpu().numpy())[0]
+                    == (int(ma[0]) * int(mb[0])) % (1 << 32))
+        pct = lambda xs, q: float(np.percentile(np.array(xs), q))  # noqa: E731
+        latency = {"request": "one 32x32->32 multiplication (2,824 gates, 120 levels) alone",
+                   "batched_p50_ms": pct(batched, 50), "batched_p99_ms": pct(batched, 99),
+                   "batched_samples": len(batched),
+                   "per_gate_p50_ms": pct(per_gate, 50), "per_gate_p99_ms": pct(per_gate, 99),
+                   "per_gate_samples": len(per_gate), "verified": ok_b and ok_p}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_gates > 0:
+        sample = OracleSample(args.cpu_gates, seed)
+        cpu = {"value": sample.rate(), "unit": "gates/s", "cores": sample.cores, "kind": "oracle",
+               "sample": sample.desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "gates_per_step": gates_step, "batch": BATCH,
+                           "width": WIDTH, "levels": 62,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu, "mul32_latency": latency, "verified": verified}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

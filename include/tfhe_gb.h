@@ -146,6 +146,57 @@ int tfhe_mul_n(tfhe_ctx *ctx, int width, const int32_t *A, const int32_t *B, int
 int tfhe_matvec(tfhe_ctx *ctx, int width, int rows, int cols, const int32_t *M,
                 const int32_t *v, int32_t *y, void *stream);
 
+/* Mixed batches: several circuit jobs of different kinds, widths and
+ * depths compiled into one level schedule, so that gates of every job that
+ * are ready at the same depth share one blind-rotation launch (the paper's
+ * compound gates and bit coalescing, section V-A, generalised across
+ * circuits).  The schedule of a given list of (kind, width, rows, cols,
+ * batch) is compiled once and cached; its level sequence is replayed as a
+ * CUDA graph. */
+typedef enum {
+    TFHE_CIRCUIT_GATE = 0,   /* one gate, opcode in `width`          */
+    TFHE_CIRCUIT_ADD = 1,    /* tfhe_add_n                           */
+    TFHE_CIRCUIT_MUL = 2,    /* tfhe_mul_n                           */
+    TFHE_CIRCUIT_MATVEC = 3  /* tfhe_matvec (rows x cols)            */
+} tfhe_circuit;
+
+typedef struct {
+    int32_t kind;           /* tfhe_circuit                                       */
+    int32_t width;          /* bit width (ADD, MUL, MATVEC) or gate opcode (GATE) */
+    int32_t rows, cols;     /* MATVEC shape; ignored otherwise                    */
+    int64_t batch;          /* independent instances                              */
+    const int32_t *in0;     /* A (GATE/ADD/MUL) or M (MATVEC), device, [batch]... */
+    const int32_t *in1;     /* B or v, device                                     */
+    int32_t *out;           /* R or y, device                                     */
+} tfhe_job;
+
+int tfhe_run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, void *stream);
+
+/* Bootstrapped-gate count and depth (levels) of one instance of a circuit;
+ * needs no context and no GPU. */
+int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, int32_t *depth);
+
+/* Context options. */
+typedef enum {
+    TFHE_OPT_GRAPHS = 0,     /* 1 (default): replay level sequences as CUDA graphs  */
+    TFHE_OPT_PER_GATE = 1,   /* 1: baseline schedule, one launch pair per gate      */
+    TFHE_OPT_PROFILE = 2     /* 1: record CUDA events around every blind-rotation   */
+                             /*    and key-switch launch of circuit schedules (also */
+                             /*    inside captured graphs)                          */
+} tfhe_option;
+
+int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);
+
+/* Kernel launches the context has issued so far (kernels inside a replayed
+ * graph count once per replay). */
+int tfhe_ctx_launches(const tfhe_ctx *ctx, uint64_t *launches);
+
+/* With TFHE_OPT_PROFILE on: device time of the blind-rotation and
+ * key-switch launches of the most recent run of every circuit schedule run
+ * since the previous call (synchronises the device, then resets). */
+int tfhe_ctx_profile(tfhe_ctx *ctx, double *br_ms, int64_t *br_launches, int64_t *br_bootstraps,
+                     double *ks_ms, int64_t *ks_launches);
+
 /* ------------------------------------------------------------------ */
 /* Client-side helpers (key generation and encryption on the device)     */
 /* ------------------------------------------------------------------ */

@@ -60,12 +60,33 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
     "tfhe_matvec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
                     + [ctypes.c_void_p] * 4),
+    "tfhe_run_jobs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]),
+    "tfhe_circuit_info": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int64),
+                                                               ctypes.POINTER(ctypes.c_int32)]),
+    "tfhe_ctx_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "tfhe_ctx_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "tfhe_ctx_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 9),
     "tfhe_encrypt_bits": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 5
                           + [ctypes.c_size_t, ctypes.c_void_p]),
     "tfhe_phase": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 3
                    + [ctypes.c_size_t, ctypes.c_void_p]),
 }
+
+GATE, ADD, MUL, MATVEC = range(4)
+OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE = 0, 1, 2
+
+
+class CJob(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("batch", ctypes.c_int64), ("in0", ctypes.c_void_p),
+                ("in1", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
 
 _lib = None
 
@@ -201,6 +222,41 @@ class Context:
         rows, cols = M.shape[0], M.shape[1]
         self._c(lib().tfhe_matvec(self._h, width, rows, cols, _dev(M, torch.int32),
                                   _dev(v, torch.int32), _dev(y, torch.int32), _stream(stream)))
+
+
+    def run_jobs(self, jobs, stream=None):
+        """jobs: list of dicts kind, width, [rows, cols], batch, in0, in1, out
+        (device tensors).  All jobs share one level schedule."""
+        arr = (CJob * len(jobs))()
+        for k, j in enumerate(jobs):
+            arr[k] = CJob(j["kind"], j["width"], j.get("rows", 0), j.get("cols", 0), j["batch"],
+                          _dev(j["in0"]).value, _dev(j["in1"]).value, _dev(j["out"]).value)
+        self._c(lib().tfhe_run_jobs(self._h, arr, len(jobs), _stream(stream)))
+
+    def set_option(self, option, value):
+        self._c(lib().tfhe_ctx_set_option(self._h, option, int(value)))
+
+    def launches(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._c(lib().tfhe_ctx_launches(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def profile(self) -> dict:
+        """Device time of blind-rotation / key-switch launches of the last
+        schedule runs (TFHE_OPT_PROFILE must be on); resets."""
+        bt, kt = ctypes.c_double(0), ctypes.c_double(0)
+        bl, bb, kl = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        self._c(lib().tfhe_ctx_profile(self._h, ctypes.byref(bt), ctypes.byref(bl),
+                                       ctypes.byref(bb), ctypes.byref(kt), ctypes.byref(kl)))
+        return dict(br_ms=bt.value, br_launches=bl.value, br_bootstraps=bb.value,
+                    ks_ms=kt.value, ks_launches=kl.value)
+
+
+def circuit_info(kind, width, rows=0, cols=0):
+    """(bootstrapped gates, depth) of one instance of a circuit."""
+    g, d = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(lib().tfhe_circuit_info(kind, width, rows, cols, ctypes.byref(g), ctypes.byref(d)))
+    return int(g.value), int(d.value)
 
 
 # ------------------------------------------------------------- client side

@@ -97,6 +97,7 @@ int run_bootstrap(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int
                          ctx->num_sms, ctx->status, stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "key switch launch");
+    ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms);
     return TFHE_OK;
 }
 
@@ -283,7 +284,10 @@ int tfhe_blind_rotate_extract(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *
     cudaError_t e = launch_blind_rotate(ctx->keys, ops, a, nullptr, (long)count, b, nullptr,
                                         (long)count, big, (long)count, kMu, ctx->status,
                                         ctx->br_grid, (cudaStream_t)stream);
-    return e == cudaSuccess ? TFHE_OK : cuda_fail(ctx, e, "blind rotation launch");
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "blind rotation launch");
+    ctx->launches += 1;
+    return TFHE_OK;
 }
 
 int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count, void *stream)
@@ -299,7 +303,18 @@ int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count
     DeviceGuard dg(ctx->device);
     cudaError_t e = launch_keyswitch(ctx->keys.ksk, big, out, nullptr, (long)count, (long)count,
                                      ctx->prm.n, ctx->num_sms, ctx->status, (cudaStream_t)stream);
-    return e == cudaSuccess ? TFHE_OK : cuda_fail(ctx, e, "key switch launch");
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "key switch launch");
+    ctx->launches += keyswitch_kernels((long)count, ctx->num_sms);
+    return TFHE_OK;
+}
+
+int tfhe_ctx_launches(const tfhe_ctx *ctx, uint64_t *launches)
+{
+    if (!ctx || !launches)
+        return TFHE_EINVAL;
+    *launches = ctx->launches;
+    return TFHE_OK;
 }
 
 int tfhe_keygen(const tfhe_params *params, const int32_t *s, const int32_t *S,

@@ -40,6 +40,7 @@ constexpr uint32_t kErrGather = 1u;
 constexpr uint32_t kErrScatter = 2u;
 constexpr uint32_t kErrTimeout = 4u;
 
+#if defined(__CUDACC__)
 // x * w mod q in [0, 2q) for any 32-bit x, with wp = floor(w 2^32 / q)
 // (Shoup's precomputed-quotient multiplication).
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t wp, uint32_t q)
@@ -61,6 +62,7 @@ __device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t
     uint32_t m = lo * qneg_inv;
     return hi + __umulhi(m, q) + (lo != 0u ? 1u : 0u);
 }
+#endif  // __CUDACC__
 
 // Per-context device pointers and sizes shared by the kernels.
 struct DevKeys {

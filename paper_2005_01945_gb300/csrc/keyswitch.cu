@@ -137,6 +137,21 @@ __global__ void __launch_bounds__(kKsThreads) k_keyswitch(const KsArgs A)
     }
 }
 
+static int ks_chunks(long count, int num_sms)
+{
+    const long tiles = (count + kKsGates - 1) / kKsGates;
+    int chunks = 1;
+    while (chunks < 32 && tiles * chunks < 2L * num_sms)
+        chunks *= 2;
+    return chunks;
+}
+
+// Kernels one launch_keyswitch call issues.
+int keyswitch_kernels(long count, int num_sms)
+{
+    return count <= 0 ? 0 : (ks_chunks(count, num_sms) > 1 ? 2 : 1);
+}
+
 // Splits the j-range so that small batches still occupy the GPU.
 cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
                              const int32_t *idx_out, long rows_out, long count, int n,
@@ -145,9 +160,7 @@ cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
     if (count <= 0)
         return cudaSuccess;
     const long tiles = (count + kKsGates - 1) / kKsGates;
-    int chunks = 1;
-    while (chunks < 32 && tiles * chunks < 2L * num_sms)
-        chunks *= 2;
+    const int chunks = ks_chunks(count, num_sms);
     KsArgs A;
     A.ksk = ksk;
     A.big = big;

@@ -4,6 +4,11 @@
 
 #include "common.cuh"
 
+namespace tgb {
+struct CircuitCache;
+struct Server;
+}  // namespace tgb
+
 struct tfhe_ctx {
     int device = 0;
     tfhe_params prm{};
@@ -18,8 +23,9 @@ struct tfhe_ctx {
     bool keys_loaded = false;
     tgb::DevKeys keys{};
     std::string err;
-    struct CircuitCache *circuits = nullptr;
-    struct Server *server = nullptr;
+    uint64_t launches = 0;           // kernels issued (graph nodes count per replay)
+    tgb::CircuitCache *circuits = nullptr;
+    tgb::Server *server = nullptr;
 };
 
 namespace tgb {
@@ -56,6 +62,8 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
 cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
                              const int32_t *idx_out, long rows_out, long count, int n,
                              int num_sms, uint32_t *status, cudaStream_t stream);
+
+int keyswitch_kernels(long count, int num_sms);
 
 void release_circuits(tfhe_ctx *ctx);
 void release_serving(tfhe_ctx *ctx);

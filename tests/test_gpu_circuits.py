@@ -1,0 +1,211 @@
+"""GPU parity of the circuit schedules through the C ABI.
+
+Bit-exact comparisons with the oracle use the real ring (N = 1024, same
+gadget and key switch) with LWE dimension n = 16, which the library takes
+at runtime; the oracle's bootstrap is then ~30x cheaper, so full-width
+32-bit circuits can be compared word for word.  Full-size workloads at
+n = 500 are checked by decryption on every output and bit-exactly on the
+outputs the oracle computes one by one (depth-1 gates on fresh inputs).
+"""
+import numpy as np
+import pytest
+
+from conftest import oparams
+from paper_2005_01945_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+class Env:
+    def __init__(self, orc, n, seed):
+        import torch
+        from paper_2005_01945_gb300 import api, build
+        build.build()
+        self.torch, self.api, self.orc = torch, api, orc
+        self.p = synth.TFHEParams(n=n)
+        self.P = oparams(self.p)
+        self.kd = synth.key_draws(self.p, seed)
+        d = api.to_device
+        kd = self.kd
+        bk, ksk = api.keygen(self.p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise),
+                             d(kd.ksk_mask), d(kd.ksk_noise))
+        self.ctx = api.Context(self.p)
+        self.ctx.set_keys(bk, ksk)
+        self.s_dev = d(kd.s)
+        self.obk = orc.keygen_bk(self.P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+        self.oksk = orc.keygen_ksk(self.P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+
+    def enc_ints(self, xs, w, seed, tag):
+        """integers -> (device [..., w, 512], oracle [..., w, n+1])"""
+        bits = synth.to_bits(xs, w)
+        cd = synth.ct_draws(self.p, bits.shape, seed, tag)
+        o = self.orc.encrypt_bits(self.P, self.kd.s, cd.mask, cd.noise, bits)
+        d = self.api.encrypt_bits(self.p, self.s_dev, self.api.to_device(cd.mask),
+                                  self.api.to_device(cd.noise), self.api.to_device(bits))
+        return d, o
+
+    def out(self, shape):
+        return self.torch.zeros(tuple(shape) + (512,), dtype=self.torch.int32, device="cuda")
+
+    def host(self, t):
+        return t.cpu().numpy().view(np.uint32)[..., :self.p.n + 1]
+
+    def dec_ints(self, o):
+        return synth.from_bits(self.orc.decrypt_bits(self.P, self.kd.s, o))
+
+
+@pytest.fixture(scope="module")
+def small(orc):
+    e = Env(orc, 16, 61)
+    yield e
+    e.ctx.close()
+
+
+@pytest.mark.parametrize("w,batch", [(1, 3), (2, 3), (5, 3), (32, 2)])
+def test_add_bit_exact(small, w, batch):
+    E = small
+    a, b = synth.int_pairs(batch, w, 1, f"add{w}")
+    da, oa = E.enc_ints(a, w, 2, f"a{w}")
+    db, ob = E.enc_ints(b, w, 2, f"b{w}")
+    R = E.out((batch, w))
+    E.ctx.add_n(w, da, db, R)
+    want, gates = E.orc.add(E.P, E.obk, E.oksk, w, oa, ob)
+    got = E.host(R)
+    assert np.array_equal(got, want)
+    assert np.array_equal(E.dec_ints(got), (a + b) % (1 << w))
+    assert E.ctx.status() == 0
+
+
+@pytest.mark.parametrize("w,batch", [(1, 2), (3, 2), (8, 2)])
+def test_mul_bit_exact(small, w, batch):
+    E = small
+    a, b = synth.int_pairs(batch, w, 3, f"mul{w}")
+    da, oa = E.enc_ints(a, w, 4, f"ma{w}")
+    db, ob = E.enc_ints(b, w, 4, f"mb{w}")
+    R = E.out((batch, w))
+    E.ctx.mul_n(w, da, db, R)
+    want, _ = E.orc.mul(E.P, E.obk, E.oksk, w, oa, ob)
+    got = E.host(R)
+    assert np.array_equal(got, want)
+    assert np.array_equal(E.dec_ints(got), (a * b) % (1 << w))
+
+
+def test_matvec_bit_exact(small):
+    E = small
+    w, rows, cols = 4, 3, 5
+    M = synth.random_uints((rows, cols), w, 5, "M")
+    v = synth.random_uints(cols, w, 5, "v")
+    dM, oM = E.enc_ints(M, w, 6, "M")
+    dv, ov = E.enc_ints(v, w, 6, "v")
+    y = E.out((rows, w))
+    E.ctx.matvec(w, dM, dv, y)
+    want, _ = E.orc.matvec(E.P, E.obk, E.oksk, w, oM, ov)
+    got = E.host(y)
+    assert np.array_equal(got, want)
+    assert np.array_equal(E.dec_ints(got), (M * v[None, :]).sum(axis=1) % (1 << w))
+
+
+def test_mixed_jobs_and_schedules_agree(small):
+    """Jobs of uneven depth share one level schedule; the result of every job
+    equals its oracle result, and equals the result of the same job run
+    alone, with graphs off, and gate by gate (one launch pair per gate)."""
+    E = small
+    api = E.api
+    a8, b8 = synth.int_pairs(2, 8, 7, "x8")
+    a4, b4 = synth.int_pairs(3, 4, 7, "x4")
+    ga, gb = synth.random_bits(5, 7, "ga"), synth.random_bits(5, 7, "gb")
+    d8a, o8a = E.enc_ints(a8, 8, 8, "x8a")
+    d8b, o8b = E.enc_ints(b8, 8, 8, "x8b")
+    d4a, o4a = E.enc_ints(a4, 4, 8, "x4a")
+    d4b, o4b = E.enc_ints(b4, 4, 8, "x4b")
+    dga, oga = E.enc_ints(ga, 1, 8, "ga")
+    dgb, ogb = E.enc_ints(gb, 1, 8, "gb")
+
+    def run(mode):
+        outs = [E.out((2, 8)), E.out((3, 4)), E.out((5, 1))]
+        jobs = [dict(kind=api.ADD, width=8, batch=2, in0=d8a, in1=d8b, out=outs[0]),
+                dict(kind=api.MUL, width=4, batch=3, in0=d4a, in1=d4b, out=outs[1]),
+                dict(kind=api.GATE, width=api.XOR, batch=5, in0=dga, in1=dgb, out=outs[2])]
+        if mode == "alone":
+            for j in jobs:
+                E.ctx.run_jobs([j])
+        else:
+            E.ctx.set_option(api.OPT_GRAPHS, mode != "nograph")
+            E.ctx.set_option(api.OPT_PER_GATE, mode == "pergate")
+            E.ctx.run_jobs(jobs)
+            E.ctx.set_option(api.OPT_GRAPHS, 1)
+            E.ctx.set_option(api.OPT_PER_GATE, 0)
+        return [E.host(o) for o in outs]
+
+    mixed = run("graph")
+    want_add, _ = E.orc.add(E.P, E.obk, E.oksk, 8, o8a, o8b)
+    want_mul, _ = E.orc.mul(E.P, E.obk, E.oksk, 4, o4a, o4b)
+    want_xor = E.orc.gates(E.P, E.obk, E.oksk, np.full(5, 3, np.uint8), oga[:, 0], ogb[:, 0])
+    assert np.array_equal(mixed[0], want_add)
+    assert np.array_equal(mixed[1], want_mul)
+    assert np.array_equal(mixed[2][:, 0], want_xor)
+    for mode in ("alone", "nograph", "pergate"):
+        other = run(mode)
+        for x, y in zip(mixed, other):
+            assert np.array_equal(x, y), mode
+
+
+# ----------------------------------------------------------- full size, n = 500
+
+@pytest.fixture(scope="module")
+def full(orc):
+    e = Env(orc, 500, synth.MASTER_SEED)
+    yield e
+    e.ctx.close()
+
+
+def test_config1_add32_x256(full):
+    """256 32-bit additions (39,424 bootstraps, depth 62): every sum decrypts
+    correctly; sampled bit-0 outputs (one XOR of fresh inputs) are bit-exact."""
+    E = full
+    a, b = synth.int_pairs(256, 32, synth.MASTER_SEED + 1, "add32")
+    da, oa = E.enc_ints(a, 32, synth.MASTER_SEED + 1, "add32a")
+    db, ob = E.enc_ints(b, 32, synth.MASTER_SEED + 1, "add32b")
+    R = E.out((256, 32))
+    E.ctx.add_n(32, da, db, R)
+    got = E.host(R)
+    assert np.array_equal(E.dec_ints(got), (a + b) % (1 << 32))
+    idx = np.array([0, 77, 255])
+    want = E.orc.gates(E.P, E.obk, E.oksk, np.full(3, 3, np.uint8), oa[idx, 0], ob[idx, 0])
+    assert np.array_equal(got[idx, 0], want)
+    assert E.ctx.status() == 0
+
+
+def test_config2_mul16_mul32_mixed(full):
+    """64 16-bit and 64 32-bit multiplications in one schedule."""
+    E = full
+    api = E.api
+    a16, b16 = synth.int_pairs(64, 16, synth.MASTER_SEED + 2, "mul16")
+    a32, b32 = synth.int_pairs(64, 32, synth.MASTER_SEED + 2, "mul32")
+    d16a, o16a = E.enc_ints(a16, 16, synth.MASTER_SEED + 2, "m16a")
+    d16b, o16b = E.enc_ints(b16, 16, synth.MASTER_SEED + 2, "m16b")
+    d32a, o32a = E.enc_ints(a32, 32, synth.MASTER_SEED + 2, "m32a")
+    d32b, o32b = E.enc_ints(b32, 32, synth.MASTER_SEED + 2, "m32b")
+    R16, R32 = E.out((64, 16)), E.out((64, 32))
+    E.ctx.run_jobs([dict(kind=api.MUL, width=16, batch=64, in0=d16a, in1=d16b, out=R16),
+                    dict(kind=api.MUL, width=32, batch=64, in0=d32a, in1=d32b, out=R32)])
+    g16, g32 = E.host(R16), E.host(R32)
+    assert np.array_equal(E.dec_ints(g16), (a16 * b16) % (1 << 16))
+    assert np.array_equal(E.dec_ints(g32), (a32 * b32) % (1 << 32))
+    idx = np.array([3, 60])
+    want = E.orc.gates(E.P, E.obk, E.oksk, np.full(2, 1, np.uint8), o32a[idx, 0], o32b[idx, 0])
+    assert np.array_equal(g32[idx, 0], want)
+
+
+def test_config3_matvec16(full):
+    """16x16 matrix times 16-vector, 16-bit (183,648 bootstraps)."""
+    E = full
+    M = synth.random_uints((16, 16), 16, synth.MASTER_SEED + 3, "M")
+    v = synth.random_uints(16, 16, synth.MASTER_SEED + 3, "v")
+    dM, _ = E.enc_ints(M, 16, synth.MASTER_SEED + 3, "M")
+    dv, _ = E.enc_ints(v, 16, synth.MASTER_SEED + 3, "v")
+    y = E.out((16, 16))
+    E.ctx.matvec(16, dM, dv, y)
+    got = E.host(y)
+    assert np.array_equal(E.dec_ints(got), (M * v[None, :]).sum(axis=1) % (1 << 16))
+    assert E.ctx.status() == 0

@@ -112,3 +112,15 @@ def test_count_table_consistent():
             assert g == mul(w)
         else:
             assert g == r * (k * mul(w) + (k - 1) * add(w))
+
+
+def test_library_netlists_match_count_table():
+    """The CUDA library's netlist builder (host code, no GPU needed) has the
+    gate counts of the circuit definitions, and the 32-bit adder's ASAP
+    depth is 2 (first XOR/AND level) + 2 per middle bit = 62."""
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    kinds = {"add": api.ADD, "mul": api.MUL, "matvec": api.MATVEC}
+    for (kind, w, r, c), g in _counts().items():
+        assert api.circuit_info(kinds[kind], w, r, c)[0] == g
+    assert api.circuit_info(api.ADD, 32)[1] == 62
