@@ -129,6 +129,26 @@ int tfhe_blind_rotate_extract(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *
                               const int32_t *b, int32_t *big, size_t count, void *stream);
 int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count, void *stream);
 
+/* Same computation and result as tfhe_bootstrap_gates, for callers that
+ * cannot let the library allocate device memory while they call it
+ * (runtimes that reserve all device memory up front, serving loops that
+ * must not hit cudaMalloc and its implicit synchronisation, hosts that
+ * account for every byte).  The paper has no counterpart; this is a
+ * deployment interface.  It calls no cudaMalloc/cudaFree or any other
+ * allocating routine: its scratch is a fixed array of
+ * TFHE_NOALLOC_MAX_GATES rows (2,162,688 bytes) in the library's device
+ * image, which every GPU that loads the library holds until the process
+ * exits.  count > TFHE_NOALLOC_MAX_GATES is rejected with TFHE_EINVAL
+ * (split the batch).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  All calls on a device share the one array: calls
+ * that overlap on the GPU (other streams, other contexts on the same
+ * device) race and must be serialised by the caller.  Nothing in the array
+ * needs clearing between calls. */
+#define TFHE_NOALLOC_MAX_GATES 512
+int tfhe_bootstrap_gates_noalloc(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a,
+                                 const int32_t *b, int32_t *out, size_t count, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Circuits over encrypted integers (bit 0 first)                        */
 /* ------------------------------------------------------------------ */

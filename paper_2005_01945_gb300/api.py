@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libtfhe_gb.so")
 LWE_STRIDE = 512
 BIG_STRIDE = 1056
 MU = 1 << 29
+NOALLOC_MAX_GATES = 512
 NAND, AND, OR, XOR, NOR, XNOR = range(6)
 GATE_NAMES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR"]
 
@@ -49,6 +50,8 @@ EXPORTS = {
     "tfhe_last_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "tfhe_ctx_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "tfhe_bootstrap_gates": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_bootstrap_gates_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t,
+                                                                           ctypes.c_void_p]),
     "tfhe_bootstrap": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_uint32,
                                                              ctypes.c_void_p]),
     "tfhe_blind_rotate_extract": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t,
@@ -185,6 +188,16 @@ class Context:
         self._c(lib().tfhe_bootstrap_gates(self._h, _dev(ops, torch.uint8), _dev(a, torch.int32),
                                            _dev(b, torch.int32), _dev(out, torch.int32), count,
                                            _stream(stream)))
+
+    def bootstrap_gates_noalloc(self, ops, a, b, out, stream=None):
+        """Like bootstrap_gates, but the library allocates nothing during the
+        call (fixed scratch of NOALLOC_MAX_GATES gates per device; calls that
+        overlap on the GPU race)."""
+        import torch
+        count = ops.numel()
+        self._c(lib().tfhe_bootstrap_gates_noalloc(
+            self._h, _dev(ops, torch.uint8), _dev(a, torch.int32), _dev(b, torch.int32),
+            _dev(out, torch.int32), count, _stream(stream)))
 
     def bootstrap(self, x, out, mu=MU, stream=None):
         import torch
