@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--cpu-gates", type=int, default=128)
     ap.add_argument("--br-only", type=int, default=0, help="profile mode: blind rotation alone")
+    ap.add_argument("--br-group", type=int, default=0, help="bootstraps per CTA (0: automatic)")
     return ap.parse_args()
 
 
@@ -179,7 +180,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_br_only(count):
+def run_br_only(count, group=0):
     """Blind rotation + extraction alone on `count` fresh gates (profiling)."""
     import torch
     from paper_2005_01945_gb300 import api, build, synth
@@ -191,6 +192,7 @@ def run_br_only(count):
                          d(kd.ksk_noise))
     ctx = api.Context(p)
     ctx.set_keys(bk, ksk)
+    ctx.set_option(api.OPT_BR_GROUP, group)
     bits = synth.random_bits((2, count), 7, "bronly")
     cd = synth.ct_draws(p, (2, count), 7, "bronly")
     s_dev = d(kd.s)
@@ -210,7 +212,7 @@ def run_br_only(count):
         torch.cuda.synchronize()
         br.append(e0.elapsed_time(e1))
         ks.append(e1.elapsed_time(e2))
-    print(json.dumps({"br_only": count, "br_ms": br, "ks_ms": ks,
+    print(json.dumps({"br_only": count, "group": group, "br_ms": br, "ks_ms": ks,
                       "bootstraps_per_s": count / (min(br) / 1e3)}), flush=True)
     ctx.close()
 
@@ -221,7 +223,7 @@ def main():
         run_reference(args)
         return
     if args.br_only:
-        run_br_only(args.br_only)
+        run_br_only(args.br_only, args.br_group)
         return
     import torch
     from paper_2005_01945_gb300 import api, build, synth

@@ -200,9 +200,11 @@ int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, i
 typedef enum {
     TFHE_OPT_GRAPHS = 0,     /* 1 (default): replay level sequences as CUDA graphs  */
     TFHE_OPT_PER_GATE = 1,   /* 1: baseline schedule, one launch pair per gate      */
-    TFHE_OPT_PROFILE = 2     /* 1: record CUDA events around every blind-rotation   */
+    TFHE_OPT_PROFILE = 2,    /* 1: record CUDA events around every blind-rotation   */
                              /*    and key-switch launch of circuit schedules (also */
                              /*    inside captured graphs)                          */
+    TFHE_OPT_BR_GROUP = 3    /* bootstraps per blind-rotation CTA: 1, 2 or 4, or 0  */
+                             /*    (default) to choose by batch size                */
 } tfhe_option;
 
 int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);

@@ -82,7 +82,7 @@ EXPORTS = {
 }
 
 GATE, ADD, MUL, MATVEC = range(4)
-OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE = 0, 1, 2
+OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP = 0, 1, 2, 3
 
 
 class CJob(ctypes.Structure):

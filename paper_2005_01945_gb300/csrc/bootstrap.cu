@@ -12,18 +12,24 @@
 // GB300 design (not the paper's: it used cuFFT in floating point):
 //  * the products are exact: a negacyclic NTT modulo two primes below 2^28
 //    and a centred CRT lift back to Z/2^32;
-//  * one CTA of 4 warps owns one bootstrap at a time and loops over gates
-//    (persistent grid); the accumulator never leaves shared memory;
-//  * warp w = (c, j) forms digit polynomial (c, j) in registers and runs the
-//    forward transforms for both primes; warp w = (p, q) then does the
-//    pointwise products with BK_i for output polynomial p modulo prime q,
-//    the inverse transform, and half of the CRT + accumulate;
+//  * one group of 4 warps owns one bootstrap; a CTA runs B in {1, 2, 4}
+//    bootstraps in lockstep (4B warps) and loops over gate groups
+//    (persistent grid); the accumulators never leave shared memory;
+//  * warp (c, h) of a bootstrap works modulo prime h for the whole CMux:
+//    it forms both digit polynomials of TLWE polynomial c (one rotation)
+//    and transforms them; then, as warp (p, h), it does the pointwise
+//    products with BK_i for output polynomial p, the inverse transform and
+//    half of the CRT + accumulate;
 //  * one 1024-point transform is one warp: 32 coefficients per lane,
 //    a 32-point transform in registers, a twiddle, one shared-memory
 //    transpose, and a second 32-point transform (four-step NTT);
+//  * code size is the binding constraint on instruction fetch: each
+//    transform exists once (the prime is a runtime value), and the warps of
+//    a CTA execute the same phase at the same time;
 //  * the bootstrapping key is pre-transformed, scaled by 2^32 N^-1 and
 //    interleaved so that lane l reads its 4 rows for one register as one
-//    16-byte load; the 33 MB key stays L2-resident across gates.
+//    16-byte load; the 33 MB key stays L2-resident across gates, and the B
+//    bootstraps of a CTA read each key row once through L1.
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -46,36 +52,44 @@ struct NttConst {
 
 __constant__ NttConst c_ntt;
 
-template <int P>
-__device__ __forceinline__ constexpr uint32_t prime() { return P == 0 ? kQ0 : kQ1; }
-
 __host__ __device__ constexpr int brv5(int k)
 {
     return ((k & 1) << 4) | ((k & 2) << 2) | (k & 4) | ((k & 8) >> 2) | ((k & 16) >> 4);
 }
 
-// 32-point Cooley-Tukey pass in registers, lazy in [0, 4q).
-// TBL 0: negacyclic (stage A) twiddles; 1: cyclic (stage D), whose first
-// twiddle of every level is 1.
-template <int P, int TBL>
-__device__ __forceinline__ void ct32(uint32_t (&x)[32])
+// The transforms take the prime as a runtime value (one of two) so that a
+// single copy of each transform serves both primes; twiddles are read from
+// the constant bank with an offset on the prime.
+struct Prime {
+    uint32_t q, q2, P;
+    __device__ __forceinline__ explicit Prime(uint32_t p)
+        : q(p ? kQ1 : kQ0), q2(2 * (p ? kQ1 : kQ0)), P(p) {}
+};
+
+// 32-point Cooley-Tukey pass in registers.
+// CYC false (stage A, negacyclic twiddles): inputs in [0, 2q); no reduction
+//   between levels, so values grow by at most 2q per level: outputs < 12q.
+// CYC true (stage D, cyclic twiddles, the first of every level is 1):
+//   Harvey's lazy butterfly, inputs and outputs in [0, 4q).
+template <bool CYC>
+__device__ __forceinline__ void ct32(uint32_t (&x)[32], const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>(), q2 = 2 * prime<P>();
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int m = 1 << s, ln = 16 >> s;
 #pragma unroll
         for (int g = 0; g < m; ++g) {
-            const uint32_t w = TBL == 0 ? c_ntt.za[P][m + g][0] : c_ntt.zd[P][m + g][0];
-            const uint32_t wp = TBL == 0 ? c_ntt.za[P][m + g][1] : c_ntt.zd[P][m + g][1];
+            const uint32_t(*tb)[32][2] = CYC ? c_ntt.zd : c_ntt.za;
+            const uint32_t w = tb[pr.P][m + g][0];
+            const uint32_t wp = tb[pr.P][m + g][1];
 #pragma unroll
             for (int jj = 0; jj < ln; ++jj) {
                 const int j = 2 * g * ln + jj;
-                const uint32_t u = csub(x[j], q2);
-                const uint32_t t = (TBL == 1 && g == 0) ? csub(x[j + ln], q2)
-                                                        : mul_shoup(x[j + ln], w, wp, q);
+                const uint32_t u = CYC ? csub(x[j], pr.q2) : x[j];
+                const uint32_t t = (CYC && g == 0) ? csub(x[j + ln], pr.q2)
+                                                   : mul_shoup(x[j + ln], w, wp, pr.q);
                 x[j] = u + t;
-                x[j + ln] = u - t + q2;
+                x[j + ln] = u - t + pr.q2;
             }
         }
     }
@@ -83,44 +97,42 @@ __device__ __forceinline__ void ct32(uint32_t (&x)[32])
 
 // Inverse (Gentleman-Sande) of ct32, inputs and outputs in [0, 2q); the
 // result is 32 times the inverse transform.
-template <int P, int TBL>
-__device__ __forceinline__ void gs32(uint32_t (&x)[32])
+template <bool CYC>
+__device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>(), q2 = 2 * prime<P>();
 #pragma unroll
     for (int s = 4; s >= 0; --s) {
         const int m = 1 << s, ln = 16 >> s;
 #pragma unroll
         for (int g = 0; g < m; ++g) {
-            const uint32_t w = TBL == 0 ? c_ntt.iza[P][m + g][0] : c_ntt.izd[P][m + g][0];
-            const uint32_t wp = TBL == 0 ? c_ntt.iza[P][m + g][1] : c_ntt.izd[P][m + g][1];
+            const uint32_t(*tb)[32][2] = CYC ? c_ntt.izd : c_ntt.iza;
+            const uint32_t w = tb[pr.P][m + g][0];
+            const uint32_t wp = tb[pr.P][m + g][1];
 #pragma unroll
             for (int jj = 0; jj < ln; ++jj) {
                 const int j = 2 * g * ln + jj;
                 const uint32_t u = x[j], v = x[j + ln];
-                x[j] = csub(u + v, q2);
-                const uint32_t d = u - v + q2;
-                x[j + ln] = (TBL == 1 && g == 0) ? csub(d, q2) : mul_shoup(d, w, wp, q);
+                x[j] = csub(u + v, pr.q2);
+                const uint32_t d = u - v + pr.q2;
+                x[j + ln] = (CYC && g == 0) ? csub(d, pr.q2) : mul_shoup(d, w, wp, pr.q);
             }
         }
     }
 }
 
 // Forward negacyclic NTT of one polynomial held by one warp.
-// In : lane l, register r holds coefficient l + 32 r, value in [0, 4q).
+// In : lane l, register r holds coefficient l + 32 r, value in [0, 2q).
 // Out: lane l, register r holds the evaluation at psi^(2 (l + 32 brv5(r)) + 1),
 //      value in [0, 4q).  sbuf: 1024 words of this warp's shared memory.
-template <int P>
 __device__ __forceinline__ void fwd_ntt(uint32_t (&x)[32], uint32_t *sbuf, int lane,
-                                        const uint2 *__restrict__ twb)
+                                        const uint2 *__restrict__ twb, const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>();
-    ct32<P, 0>(x);
-    const uint2 *tw = twb + (P * 2 + 0) * 1024 + lane;
+    ct32<false>(x, pr);
+    const uint2 *tw = twb + (pr.P * 2 + 0) * 1024 + lane;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < 32; ++r) {   // any 32-bit input -> [0, 2q)
         const uint2 t = __ldg(tw + r * 32);
-        x[r] = mul_shoup(x[r], t.x, t.y, q);
+        x[r] = mul_shoup(x[r], t.x, t.y, pr.q);
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
@@ -132,23 +144,21 @@ __device__ __forceinline__ void fwd_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
     for (int i1 = 0; i1 < 32; ++i1)
         x[i1] = sbuf[lane * 32 + (i1 ^ lane)];
     __syncwarp();
-    ct32<P, 1>(x);
+    ct32<true>(x, pr);
 }
 
 // Inverse of fwd_ntt up to the factor N: input layout of fwd_ntt's output
 // with values in [0, 2q); output lane l, register r = N * coefficient
 // l + 32 r, in [0, 2q).
-template <int P>
 __device__ __forceinline__ void inv_ntt(uint32_t (&x)[32], uint32_t *sbuf, int lane, int lane_brv,
-                                        const uint2 *__restrict__ twb)
+                                        const uint2 *__restrict__ twb, const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>();
-    gs32<P, 1>(x);
-    const uint2 *tw = twb + (P * 2 + 1) * 1024 + lane;
+    gs32<true>(x, pr);
+    const uint2 *tw = twb + (pr.P * 2 + 1) * 1024 + lane;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
         const uint2 t = __ldg(tw + r * 32);
-        x[r] = mul_shoup(x[r], t.x, t.y, q);
+        x[r] = mul_shoup(x[r], t.x, t.y, pr.q);
     }
 #pragma unroll
     for (int r = 0; r < 32; ++r)
@@ -158,7 +168,7 @@ __device__ __forceinline__ void inv_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
     for (int r = 0; r < 32; ++r)
         x[r] = sbuf[lane * 32 + (r ^ lane)];
     __syncwarp();
-    gs32<P, 0>(x);
+    gs32<false>(x, pr);
 }
 
 // ---------------------------------------------------------------------
@@ -186,10 +196,7 @@ __global__ void __launch_bounds__(128) k_bk_to_ntt(const int32_t *__restrict__ b
         int64_t m = v % (int64_t)q;
         x[k] = (uint32_t)(m < 0 ? m + q : m);
     }
-    if (qsel == 0)
-        fwd_ntt<0>(x, sbuf[warp], lane, twb);
-    else
-        fwd_ntt<1>(x, sbuf[warp], lane, twb);
+    fwd_ntt(x, sbuf[warp], lane, twb, Prime((uint32_t)qsel));
     const uint32_t sc = c_ntt.bk_scale[qsel][0], scp = c_ntt.bk_scale[qsel][1];
     // element index in uint32 words: ((((i*2+p)*2+q)*32 + reg)*32 + lane)*4 + r
     uint32_t *dst = out + ((((i * 2 + p) * 2 + qsel) * 32) * 32 + lane) * 4 + r;
@@ -217,70 +224,100 @@ struct BrArgs {
     uint32_t *status;
 };
 
-struct BrSmem {
+struct BrSmem {                 // one bootstrap
     uint32_t acc[2][kN];        // TLWE accumulator (a(X), b(X))
     uint32_t fwd[4][2][kN];     // forward outputs [digit][prime][reg*32+lane]
     uint16_t abar[kLweStride];  // mod-switched mask and body
 };
 
-constexpr int kBrThreads = 128;
-
-// Phase 2: pointwise products for output polynomial p modulo prime P,
-// summed over the 4 digit rows; result in [0, 2q).
-template <int P>
-__device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
-                                             const uint4 *__restrict__ bkp, int lane)
+// Phase 1: warp (c, h) forms both digit polynomials of TLWE polynomial c of
+// X^a acc - acc (one rotation, two digit extractions) and transforms them
+// modulo prime h; results go to S.fwd[2c + j][h].  One transform copy: the
+// two digits are a rolled loop.
+__device__ __forceinline__ void br_digits_fwd(uint32_t (&x)[32], BrSmem &S, int c, int a,
+                                              int lane, const uint2 *__restrict__ twb,
+                                              const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>();
-    const uint32_t qn = c_ntt.qneg_inv[P];
+    const uint32_t *ac = S.acc[c];
+    uint32_t *s0 = S.fwd[2 * c][pr.P], *s1 = S.fwd[2 * c + 1][pr.P];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int k = lane + 32 * r;
+        const int idx = (k - a) & (2 * kN - 1);
+        uint32_t v = ac[idx & (kN - 1)];
+        v = idx >= kN ? 0u - v : v;
+        const uint32_t u = v - ac[k] + kDecompOffset;
+        x[r] = ((u >> 22) & 1023u) + (pr.q - 512u);            // level-0 digit + q
+        s1[r * 32 + lane] = ((u >> 12) & 1023u) + (pr.q - 512u);  // level-1 digit, parked
+    }
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+        uint32_t *sj = j ? s1 : s0;
+        if (j) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                x[r] = s1[r * 32 + lane];
+            __syncwarp();
+        }
+        fwd_ntt(x, sj, lane, twb, pr);
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            sj[r * 32 + lane] = x[r];
+    }
+}
+
+// Phase 2: pointwise products for output polynomial p modulo prime h,
+// summed over the 4 digit rows; result in [0, 2q).
+__device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
+                                             const uint4 *__restrict__ bkp, int lane,
+                                             const Prime &pr)
+{
+    const uint32_t qn = c_ntt.qneg_inv[pr.P];
+    const uint32_t *f0 = S.fwd[0][pr.P], *f1 = S.fwd[1][pr.P], *f2 = S.fwd[2][pr.P],
+                   *f3 = S.fwd[3][pr.P];
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
         const uint4 b = __ldg(bkp + r * 32 + lane);
         const int e = r * 32 + lane;
-        uint64_t s = (uint64_t)S.fwd[0][P][e] * b.x;
-        s += (uint64_t)S.fwd[1][P][e] * b.y;
-        s += (uint64_t)S.fwd[2][P][e] * b.z;
-        s += (uint64_t)S.fwd[3][P][e] * b.w;
-        x[r] = mont_reduce(s, q, qn);
+        uint64_t s = (uint64_t)f0[e] * b.x;
+        s += (uint64_t)f1[e] * b.y;
+        s += (uint64_t)f2[e] * b.z;
+        s += (uint64_t)f3[e] * b.w;
+        x[r] = mont_reduce(s, pr.q, qn);
     }
 }
 
-// Phase 3: inverse transform, reduce to [0, q), publish the half of the
-// residues the partner warp needs for the CRT.
-template <int P>
-__device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int warp, int lane,
-                                           int lane_brv, const uint2 *__restrict__ twb)
+// Phase 3: inverse transform, reduce to [0, q), publish all residues for
+// the CRT (this warp's exchange slot).
+__device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4, int lane,
+                                           int lane_brv, const uint2 *__restrict__ twb,
+                                           const Prime &pr)
 {
-    constexpr uint32_t q = prime<P>();
-    inv_ntt<P>(x, S.fwd[warp][0], lane, lane_brv, twb);
-    uint32_t *xch = S.fwd[warp][1];
+    inv_ntt(x, S.fwd[w4][0], lane, lane_brv, twb, pr);
+    uint32_t *xch = S.fwd[w4][1];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        x[r] = csub(x[r], q);
-        if ((P == 0 && r >= 16) || (P == 1 && r < 16))
-            xch[r * 32 + lane] = x[r];
-    }
+    for (int r = 0; r < 32; ++r)
+        xch[r * 32 + lane] = csub(x[r], pr.q);
 }
 
 // Phase 4: CRT of (r0 mod q0, r1 mod q1) to the centred integer, mod 2^32,
-// added into the accumulator.  Warp (p, 0) does registers 0..15,
-// warp (p, 1) registers 16..31.
-template <int P>
-__device__ __forceinline__ void br_crt(const uint32_t (&x)[32], BrSmem &S, int p, int lane)
+// added into the accumulator.  Warp (p, h) does registers 16h .. 16h + 15.
+// Garner: u = (r1 - r0) q0^-1 mod q1, v = r0 + q0 u in [0, q0 q1); v is
+// centred (v - q0 q1) when v >= (q0 q1 + 1)/2, which for r0 < q0 holds iff
+// u > (q1 - 1)/2, or u = (q1 - 1)/2 and r0 >= (q0 + 1)/2.
+__device__ __forceinline__ void br_crt(BrSmem &S, int p, int h, int lane)
 {
-    const uint32_t *other = S.fwd[p * 2 + (1 - P)][1];
+    const uint32_t *x0 = S.fwd[p * 2 + 0][1], *x1 = S.fwd[p * 2 + 1][1];
     const uint32_t c = c_ntt.crt_c, cp = c_ntt.crt_cp, plo = c_ntt.p_lo;
-    const uint64_t phalf = c_ntt.p_half;
+    constexpr uint32_t uh = (kQ1 - 1) / 2, rh = (kQ0 + 1) / 2;
+    uint32_t *acc = S.acc[p];
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
-        const int r = P == 0 ? rr : rr + 16;
-        const uint32_t r0 = P == 0 ? x[r] : other[r * 32 + lane];
-        const uint32_t r1 = P == 0 ? other[r * 32 + lane] : x[r];
-        uint32_t u = mul_shoup(r1 - r0 + 2 * kQ1, c, cp, kQ1);
-        u = csub(u, kQ1);
-        const uint64_t v = (uint64_t)r0 + (uint64_t)kQ0 * u;
-        const uint32_t res = (uint32_t)v - (v >= phalf ? plo : 0u);
-        S.acc[p][lane + 32 * r] += res;
+        const int e = (16 * h + rr) * 32 + lane;
+        const uint32_t r0 = x0[e], r1 = x1[e];
+        const uint32_t u = csub(mul_shoup(r1 - r0 + 2 * kQ1, c, cp, kQ1), kQ1);
+        const bool neg = u > uh || (u == uh && r0 >= rh);
+        acc[e] += r0 + kQ0 * u - (neg ? plo : 0u);
     }
 }
 
@@ -296,44 +333,59 @@ __device__ __forceinline__ void gate_consts(int op, uint32_t &mu, uint32_t &alph
     }
 }
 
-__global__ void __launch_bounds__(kBrThreads) k_blind_rotate(const BrArgs A)
+// B bootstraps per CTA (4B warps); 128 registers per thread, 16 warps/SM.
+template <int B>
+__global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
 {
     extern __shared__ uint4 smem_raw[];
-    BrSmem &S = *reinterpret_cast<BrSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bi = warp >> 2, w4 = warp & 3, tb = tid & 127;  // bootstrap slot, role
+    BrSmem &S = reinterpret_cast<BrSmem *>(smem_raw)[bi];
     const int lane_brv = brv5(lane);
     const int n = A.keys.n;
+    const int p = w4 >> 1, h = w4 & 1;
+    const Prime pr((uint32_t)h);
 
-    for (long g = blockIdx.x; g < A.count; g += gridDim.x) {
-        // ---- gate combine + mod switch (fused prologue)
-        const long ra = A.idx_a ? (long)A.idx_a[g] : g;
-        const long rb = A.ops ? (A.idx_b ? (long)A.idx_b[g] : g) : 0;
-        const bool ok = ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b));
-        if (!ok) {
-            if (tid == 0)
-                atomicOr(A.status, kErrGather);
-            int32_t *bg = A.big + g * kBigStride;
-            for (int k = tid; k <= kN; k += kBrThreads)
-                bg[k] = 0;
-            continue;  // uniform across the CTA
+    for (long grp = blockIdx.x; grp * B < A.count; grp += gridDim.x) {
+        const long g = grp * B + bi;
+        // ---- gate combine + mod switch (fused prologue); an empty or bad
+        // slot runs with abar = 0 and writes nothing (bad: zero row + flag)
+        bool active = g < A.count;
+        long ra = 0, rb = 0;
+        if (active) {
+            ra = A.idx_a ? (long)A.idx_a[g] : g;
+            rb = A.ops ? (A.idx_b ? (long)A.idx_b[g] : g) : 0;
+            if (!(ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b)))) {
+                if (tb == 0)
+                    atomicOr(A.status, kErrGather);
+                int32_t *bg = A.big + g * kBigStride;
+                for (int k = tb; k <= kN; k += 128)
+                    bg[k] = 0;
+                active = false;
+            }
         }
-        const int32_t *ca = A.in_a + ra * kLweStride;
-        const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
-        uint32_t mu_g = 0, alpha = 1;
-        if (A.ops)
-            gate_consts(A.ops[g], mu_g, alpha);
-        for (int i = tid; i <= n; i += kBrThreads) {
-            uint32_t c = A.ops ? alpha * ((uint32_t)ca[i] + (uint32_t)cb[i]) : (uint32_t)ca[i];
-            if (i == n)
-                c += mu_g;
-            S.abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
+        if (active) {
+            const int32_t *ca = A.in_a + ra * kLweStride;
+            const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
+            uint32_t mu_g = 0, alpha = 1;
+            if (A.ops)
+                gate_consts(A.ops[g], mu_g, alpha);
+            for (int i = tb; i <= n; i += 128) {
+                uint32_t c = A.ops ? alpha * ((uint32_t)ca[i] + (uint32_t)cb[i]) : (uint32_t)ca[i];
+                if (i == n)
+                    c += mu_g;
+                S.abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
+            }
+        } else {
+            for (int i = tb; i <= n; i += 128)
+                S.abar[i] = 0;
         }
         __syncthreads();
 
         // ---- acc = (0, X^(-bbar) v)
         {
             const int m = (2 * kN - (int)S.abar[n]) & (2 * kN - 1);
-            for (int k = tid; k < kN; k += kBrThreads) {
+            for (int k = tb; k < kN; k += 128) {
                 bool pos = k >= (m & (kN - 1));
                 if (m >= kN)
                     pos = !pos;
@@ -343,68 +395,35 @@ __global__ void __launch_bounds__(kBrThreads) k_blind_rotate(const BrArgs A)
         }
         __syncthreads();
 
-        // ---- n CMux steps
+        // ---- n CMux steps, all B bootstraps in lockstep
+        const BrSmem *all = reinterpret_cast<const BrSmem *>(smem_raw);
         for (int i = 0; i < n; ++i) {
-            const int a = S.abar[i];
-            if (a == 0)
-                continue;  // X^0 acc - acc = 0: the step leaves acc unchanged
+            int any = 0;
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                any |= all[b].abar[i];
+            if (any == 0)
+                continue;  // X^0 acc - acc = 0 for every slot: nothing changes
+            const int a = S.abar[i];  // a = 0 here gives zero digits: acc unchanged
             uint32_t x[32];
-            {   // phase 1: warp (c, j) builds digit polynomial c*l + j, both NTTs
-                const int c = warp >> 1, shift = 22 - 10 * (warp & 1);
-                const uint32_t *ac = S.acc[c];
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    const int k = lane + 32 * r;
-                    const int idx = (k - a) & (2 * kN - 1);
-                    uint32_t v = ac[idx & (kN - 1)];
-                    v = idx >= kN ? 0u - v : v;
-                    const uint32_t u = v - ac[k] + kDecompOffset;
-                    x[r] = (u >> shift) & 1023u;  // digit + 512
-                }
-                uint32_t *s0 = S.fwd[warp][0], *s1 = S.fwd[warp][1];
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    s1[r * 32 + lane] = x[r];
-                    x[r] += kQ0 - 512u;
-                }
-                fwd_ntt<0>(x, s0, lane, A.keys.twb);
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    s0[r * 32 + lane] = x[r];
-                    x[r] = s1[r * 32 + lane] + (kQ1 - 512u);
-                }
-                __syncwarp();
-                fwd_ntt<1>(x, s1, lane, A.keys.twb);
-#pragma unroll
-                for (int r = 0; r < 32; ++r)
-                    s1[r * 32 + lane] = x[r];
-            }
+            br_digits_fwd(x, S, p, a, lane, A.keys.twb, pr);
             __syncthreads();
-            const int p = warp >> 1, qs = warp & 1;
-            const uint4 *bkp = A.keys.bk_ntt + (((long)i * 2 + p) * 2 + qs) * 1024;
-            if (qs == 0)
-                br_pointwise<0>(x, S, bkp, lane);
-            else
-                br_pointwise<1>(x, S, bkp, lane);
+            br_pointwise(x, S, A.keys.bk_ntt + (((long)i * 2 + p) * 2 + h) * 1024, lane, pr);
             __syncthreads();
-            if (qs == 0)
-                br_inverse<0>(x, S, warp, lane, lane_brv, A.keys.twb);
-            else
-                br_inverse<1>(x, S, warp, lane, lane_brv, A.keys.twb);
+            br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
             __syncthreads();
-            if (qs == 0)
-                br_crt<0>(x, S, p, lane);
-            else
-                br_crt<1>(x, S, p, lane);
+            br_crt(S, p, h, lane);
             __syncthreads();
         }
 
         // ---- sample extraction of coefficient 0
-        int32_t *bg = A.big + g * kBigStride;
-        for (int k = tid; k < kN; k += kBrThreads)
-            bg[k] = (int32_t)(k == 0 ? S.acc[0][0] : 0u - S.acc[0][kN - k]);
-        if (tid == 0)
-            bg[kN] = (int32_t)S.acc[1][0];
+        if (active) {
+            int32_t *bg = A.big + g * kBigStride;
+            for (int k = tb; k < kN; k += 128)
+                bg[k] = (int32_t)(k == 0 ? S.acc[0][0] : 0u - S.acc[0][kN - k]);
+            if (tb == 0)
+                bg[kN] = (int32_t)S.acc[1][0];
+        }
         __syncthreads();
     }
 }
@@ -525,7 +544,54 @@ cudaError_t launch_bk_to_ntt(const int32_t *bk_dev, uint32_t *bk_ntt, int n, con
     return cudaGetLastError();
 }
 
-size_t br_smem_bytes() { return sizeof(BrSmem); }
+template <int B>
+static void br_prepare()
+{
+    cudaFuncSetAttribute(k_blind_rotate<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(B * sizeof(BrSmem)));
+    cudaFuncSetAttribute(k_blind_rotate<B>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    (void)cudaGetLastError();
+}
+
+template <int B>
+static int br_blocks(int dev)
+{
+    static int cached[64] = {0};
+    if (dev < 0 || dev >= 64)
+        return 1;
+    if (!cached[dev]) {
+        br_prepare<B>();
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B>, 128 * B,
+                                                          B * sizeof(BrSmem)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            nb = 0;
+        }
+        cached[dev] = nb > 0 ? nb : 1;
+    }
+    return cached[dev];
+}
+
+// Bootstraps in flight per SM for the variant (all variants: 16 warps).
+int br_blocks_per_sm()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    br_blocks<2>(dev);
+    br_blocks<4>(dev);
+    return br_blocks<1>(dev);
+}
+
+// Lockstep group size: several bootstraps per CTA share instruction fetch
+// and key reads, but leave SMs idle when a level is narrow.
+static int br_group(long count, int num_sms, int forced)
+{
+    if (forced == 1 || forced == 2 || forced == 4)
+        return forced;
+    const long per_sm = (count + num_sms - 1) / num_sms;
+    return per_sm >= 8 ? 4 : (per_sm >= 3 ? 2 : 1);
+}
 
 cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const int32_t *in_a,
                                 const int32_t *idx_a, long rows_a, const int32_t *in_b,
@@ -547,22 +613,23 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     A.count = count;
     A.mu = mu;
     A.status = status;
-    const unsigned blocks = (unsigned)(count < grid ? count : grid);
-    k_blind_rotate<<<blocks, kBrThreads, sizeof(BrSmem), stream>>>(A);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int B = br_group(count, sms > 0 ? sms : 1, keys.br_group);
+    const long groups = (count + B - 1) / B;
+    long blocks_per_sm = B == 4 ? br_blocks<4>(dev) : (B == 2 ? br_blocks<2>(dev) : br_blocks<1>(dev));
+    const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
+    const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
+    (void)grid;
+    switch (B) {
+    case 4: k_blind_rotate<4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
+    case 2: k_blind_rotate<2><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
+    default: k_blind_rotate<1><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
+    }
     return cudaGetLastError();
 }
 
 }  // namespace tgb
 
-namespace tgb {
-int br_blocks_per_sm()
-{
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate, kBrThreads,
-                                                      sizeof(BrSmem)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        nb = 1;
-    }
-    return nb > 0 ? nb : 1;
-}
-}  // namespace tgb

@@ -615,6 +615,16 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
     case TFHE_OPT_PROFILE:
         C.profile = value != 0;
         return TFHE_OK;
+    case TFHE_OPT_BR_GROUP:
+        if (value != 0 && value != 1 && value != 2 && value != 4)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2 or 4");
+        ctx->keys.br_group = (int)value;
+        for (auto &kv : C.plans)   // captured graphs hold the old launch shape
+            if (kv.second->graph) {
+                cudaGraphExecDestroy(kv.second->graph);
+                kv.second->graph = nullptr;
+            }
+        return TFHE_OK;
     default:
         return fail(ctx, TFHE_EINVAL, "unknown option %d", option);
     }

@@ -70,6 +70,7 @@ struct DevKeys {
     const uint4 *ksk;      // [N][t][base-1][kLweStride/4] words
     const uint2 *twb;      // stage-B twiddles [2 prime][2 dir][32 reg][32 lane] (w, w')
     int n;
+    int br_group;          // bootstraps per blind-rotation CTA: 1, 2, 4, or 0 = by batch size
 };
 
 }  // namespace tgb

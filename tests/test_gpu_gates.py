@@ -177,3 +177,21 @@ def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
     sample = synth._gen(31, "sample").choice(count, 12, replace=False)
     want = orc.gates(P, gpu["obk"], gpu["oksk"], ops[sample], cts[0][sample], cts[1][sample])
     assert np.array_equal(got[sample, :p.n + 1], want)
+
+
+@pytest.mark.parametrize("group", [1, 2, 4])
+def test_each_lockstep_group_bit_exact(gpu, orc, group):
+    """Blind rotation with 1, 2 or 4 bootstraps per CTA: 13 gates leave empty
+    slots in the last group (and skipped CMux steps in some slots)."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    count = 13
+    bits, cts, dev = _fresh(gpu, orc, count, 40 + group, f"grp{group}", zero_some=True)
+    ops = ((np.arange(count) * 5) % 6).astype(np.uint8)
+    out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].set_option(api.OPT_BR_GROUP, group)
+    try:
+        gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+    finally:
+        gpu["ctx"].set_option(api.OPT_BR_GROUP, 0)
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
+    assert np.array_equal(_u32(out)[:, :p.n + 1], want)
