@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--cpu-gates", type=int, default=128)
     ap.add_argument("--br-only", type=int, default=0, help="profile mode: blind rotation alone")
     ap.add_argument("--br-group", type=int, default=0, help="bootstraps per CTA (0: automatic)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload: Poisson requests at 3 rates (config 4)")
+    ap.add_argument("--serve-requests", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -217,6 +220,112 @@ def run_br_only(count, group=0):
     ctx.close()
 
 
+SERVE_KINDS = [("gate", 0, 1), ("add16", 1, 16), ("add32", 1, 32), ("mul16", 2, 16),
+               ("mul32", 2, 32)]
+
+
+def run_serve(args):
+    """Config 4: a Poisson request stream at 0.3, 0.6 and 0.9 of the measured
+    saturated request rate, requests drawn uniformly from {single gate,
+    16-bit add, 32-bit add, 16-bit mul, 32-bit mul}; keys device-resident,
+    admission by pool memory, gates batched across requests per level."""
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    seed = synth.MASTER_SEED + 4
+    kd = synth.key_draws(p, seed)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    s_dev = d(kd.s)
+    variants = 8
+    inputs = {}   # per kind: (A, B, plaintexts) with `variants` distinct operands
+    for name, kind, w in SERVE_KINDS:
+        a, b = synth.int_pairs(variants, w, seed, name)
+        ba, bb = synth.to_bits(a, w), synth.to_bits(b, w)
+        ca = synth.ct_draws(p, ba.shape, seed, name + "a")
+        cb = synth.ct_draws(p, bb.shape, seed, name + "b")
+        inputs[name] = (api.encrypt_bits(p, s_dev, d(ca.mask), d(ca.noise), d(ba)),
+                        api.encrypt_bits(p, s_dev, d(cb.mask), d(cb.noise), d(bb)), a, b)
+    gates_of = {name: (1 if kind == 0 else api.circuit_info(kind, w)[0])
+                for name, kind, w in SERVE_KINDS}
+
+    def run_stream(arrivals, kinds, budget=32 << 30):
+        n = len(arrivals)
+        outs = {name: torch.empty((max(1, int((kinds == k).sum())), w, api.LWE_STRIDE),
+                                  dtype=torch.int32, device="cuda")
+                for k, (name, kind, w) in enumerate(SERVE_KINDS)}
+        used = {name: 0 for name, _, _ in SERVE_KINDS}
+        ctx.serve_start(budget)
+        ids, meta = [], []
+        t0 = time.perf_counter()
+        for t_arr, k in zip(arrivals, kinds):
+            name, kind, w = SERVE_KINDS[k]
+            while time.perf_counter() - t0 < t_arr:
+                time.sleep(0.0002)
+            A, B, _, _ = inputs[name]
+            v = len(ids) % variants
+            slot = used[name]
+            used[name] += 1
+            out = outs[name][slot]
+            width = 3 if kind == 0 else w          # a single gate is an XOR
+            ids.append(ctx.serve_submit(kind, width, A[v], B[v], out))
+            meta.append((name, v, slot))
+        lats = np.array([ctx.serve_wait(i, 600000) for i in ids])
+        stats = ctx.serve_stats()
+        ctx.serve_stop()
+        torch.cuda.synchronize()
+        # verify the multiplications of the stream by decryption
+        ok = True
+        for name in ("mul32", "add32"):
+            _, _, a, b = inputs[name]
+            w = 32
+            k = used[name]
+            if k == 0:
+                continue
+            dec = synth.from_bits(api.decrypt_bits(p, s_dev, outs[name][:k]).cpu().numpy())
+            vs = np.array([v for (nm, v, _) in meta if nm == name])
+            want = (a[vs] * b[vs] if name == "mul32" else a[vs] + b[vs]) % (1 << w)
+            ok &= bool(np.array_equal(dec, want))
+        wall = stats["wall_ms"] / 1e3
+        return lats, stats, wall, ok, [m[0] for m in meta]
+
+    # saturated capacity: a burst of requests all at once
+    rng = np.random.default_rng(seed)
+    burst = 200
+    kinds = rng.integers(0, len(SERVE_KINDS), size=burst)
+    lats, stats, wall, ok, _ = run_stream(np.zeros(burst), kinds)
+    cap_gates = stats["gates"] / wall
+    mean_gates = float(np.mean([gates_of[n] for n, _, _ in SERVE_KINDS]))
+    cap_req = cap_gates / mean_gates
+    results = []
+    per_rate = args.serve_requests // 3
+    for frac in (0.3, 0.6, 0.9):
+        lam = frac * cap_req
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=per_rate))
+        kinds = rng.integers(0, len(SERVE_KINDS), size=per_rate)
+        lats, stats, wall, ok, names = run_stream(arr, kinds)
+        names = np.array(names)
+        m32 = lats[names == "mul32"]
+        results.append({"load": frac, "offered_req_per_s": lam, "requests": per_rate,
+                        "gates_per_s": stats["gates"] / wall, "iterations": stats["iterations"],
+                        "p50_ms": float(np.percentile(lats, 50)),
+                        "p99_ms": float(np.percentile(lats, 99)),
+                        "mul32_p50_ms": float(np.percentile(m32, 50)) if len(m32) else None,
+                        "mul32_p99_ms": float(np.percentile(m32, 99)) if len(m32) else None,
+                        "verified": ok})
+    print(json.dumps({"metric": "serving: p50/p99 request latency and gates/s under Poisson load",
+                      "config": {"workload": "config 4: requests uniform over {XOR gate, add16, "
+                                             "add32, mul16, mul32}; mean 740.2 gates/request",
+                                 "capacity_gates_per_s": cap_gates,
+                                 "capacity_req_per_s": cap_req},
+                      "rates": results}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -224,6 +333,9 @@ def main():
         return
     if args.br_only:
         run_br_only(args.br_only, args.br_group)
+        return
+    if args.serve:
+        run_serve(args)
         return
     import torch
     from paper_2005_01945_gb300 import api, build, synth

@@ -220,6 +220,60 @@ int tfhe_ctx_profile(tfhe_ctx *ctx, double *br_ms, int64_t *br_launches, int64_t
                      double *ks_ms, int64_t *ks_launches);
 
 /* ------------------------------------------------------------------ */
+/* Serving: continuous batching of requests                              */
+/* ------------------------------------------------------------------ */
+
+/* One request: one instance of a circuit (kind/width/rows/cols as in
+ * tfhe_job, batch 1).  in0/in1/out are device buffers owned by the caller
+ * and must stay valid until the request completes. */
+typedef struct {
+    int32_t kind, width, rows, cols;
+    const int32_t *in0, *in1;
+    int32_t *out;
+} tfhe_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t gates;          /* bootstraps run                               */
+    uint64_t iterations;     /* batched launches (one level of many requests) */
+    uint64_t in_flight;      /* admitted, not finished                       */
+    uint64_t queued;         /* waiting for pool rows                        */
+    double wall_ms;          /* first submit to last completion              */
+} tfhe_serve_info;
+
+/* Start the request loop on the context's device: a worker thread with its
+ * own stream and a ciphertext pool of hbm_budget_bytes (requests are
+ * admitted, in arrival order, when their rows fit).  Each iteration runs the
+ * next level of every admitted request as one batched bootstrap, up to
+ * max_batch_gates gates (0: a default of 8 waves of the GPU); requests that
+ * arrive meanwhile join the next iteration.  While serving, the context
+ * must not be used for other evaluation calls.  The paper's GPU framework
+ * evaluates one circuit at a time; this is its level batching (section
+ * V-A) extended across requests. */
+int tfhe_serve_start(tfhe_ctx *ctx, size_t hbm_budget_bytes, size_t max_batch_gates);
+
+/* Thread-safe.  *id identifies the request. */
+int tfhe_serve_submit(tfhe_ctx *ctx, const tfhe_request *req, uint64_t *id);
+
+/* *state: 1 done, 0 pending, < 0 failed with that tfhe_status.
+ * *latency_ms (may be NULL): submit-to-completion host time when done. */
+int tfhe_serve_poll(tfhe_ctx *ctx, uint64_t id, int *state, double *latency_ms);
+
+/* Block up to timeout_ms for completion: TFHE_OK, TFHE_ETIMEOUT or the
+ * request's failure status. */
+int tfhe_serve_wait(tfhe_ctx *ctx, uint64_t id, int timeout_ms, double *latency_ms);
+
+int tfhe_serve_stats(tfhe_ctx *ctx, tfhe_serve_info *out);
+
+/* Latencies (ms) of completed requests in completion order; *count gets the
+ * total, at most cap are copied. */
+int tfhe_serve_latencies(tfhe_ctx *ctx, double *ms, size_t cap, size_t *count);
+
+/* Drain queued and in-flight requests, stop the worker, free the pool.
+ * Returns TFHE_OK or the error that stopped serving. */
+int tfhe_serve_stop(tfhe_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
 /* Client-side helpers (key generation and encryption on the device)     */
 /* ------------------------------------------------------------------ */
 

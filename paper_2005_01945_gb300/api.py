@@ -74,6 +74,18 @@ EXPORTS = {
                                         ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]),
+    "tfhe_serve_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t]),
+    "tfhe_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "tfhe_serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "tfhe_serve_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "tfhe_serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tfhe_serve_latencies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t)]),
+    "tfhe_serve_stop": (ctypes.c_int, [ctypes.c_void_p]),
     "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 9),
     "tfhe_encrypt_bits": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 5
                           + [ctypes.c_size_t, ctypes.c_void_p]),
@@ -89,6 +101,18 @@ class CJob(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("rows", ctypes.c_int32),
                 ("cols", ctypes.c_int32), ("batch", ctypes.c_int64), ("in0", ctypes.c_void_p),
                 ("in1", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class CRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("in0", ctypes.c_void_p), ("in1", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
+class CServeInfo(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "gates",
+                                               "iterations", "in_flight", "queued")] + \
+               [("wall_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -263,6 +287,46 @@ class Context:
                                        ctypes.byref(bb), ctypes.byref(kt), ctypes.byref(kl)))
         return dict(br_ms=bt.value, br_launches=bl.value, br_bootstraps=bb.value,
                     ks_ms=kt.value, ks_launches=kl.value)
+
+
+    # ---- serving (continuous batching)
+
+    def serve_start(self, hbm_budget_bytes, max_batch_gates=0):
+        self._c(lib().tfhe_serve_start(self._h, int(hbm_budget_bytes), int(max_batch_gates)))
+
+    def serve_submit(self, kind, width, in0, in1, out, rows=0, cols=0) -> int:
+        req = CRequest(kind, width, rows, cols, _dev(in0).value, _dev(in1).value,
+                       _dev(out).value)
+        rid = ctypes.c_uint64(0)
+        self._c(lib().tfhe_serve_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def serve_poll(self, rid):
+        st, lat = ctypes.c_int(0), ctypes.c_double(0)
+        self._c(lib().tfhe_serve_poll(self._h, rid, ctypes.byref(st), ctypes.byref(lat)))
+        return int(st.value), float(lat.value)
+
+    def serve_wait(self, rid, timeout_ms=60000) -> float:
+        lat = ctypes.c_double(0)
+        self._c(lib().tfhe_serve_wait(self._h, rid, int(timeout_ms), ctypes.byref(lat)))
+        return float(lat.value)
+
+    def serve_stats(self) -> dict:
+        info = CServeInfo()
+        self._c(lib().tfhe_serve_stats(self._h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in CServeInfo._fields_}
+
+    def serve_latencies(self) -> np.ndarray:
+        n = ctypes.c_size_t(0)
+        self._c(lib().tfhe_serve_latencies(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.float64)
+        if n.value:
+            self._c(lib().tfhe_serve_latencies(self._h, ctypes.c_void_p(out.ctypes.data),
+                                               n.value, ctypes.byref(n)))
+        return out
+
+    def serve_stop(self):
+        self._c(lib().tfhe_serve_stop(self._h))
 
 
 def circuit_info(kind, width, rows=0, cols=0):

@@ -22,9 +22,11 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
+#include "netlist.h"
 #include "runtime.h"
 
 namespace tgb {
@@ -32,37 +34,6 @@ namespace tgb {
 // ---------------------------------------------------------------------
 // Netlists
 // ---------------------------------------------------------------------
-
-struct Netlist {
-    int n_in = 0;                    // wires [0, n_in) are inputs
-    std::vector<uint8_t> op;         // gate g drives wire n_in + g
-    std::vector<int32_t> a, b;       // input wires of every gate
-    std::vector<int32_t> out;        // output wires in output order
-    std::vector<int32_t> level;      // ASAP level of every gate (>= 1)
-    int depth = 0;
-
-    int gate(int o, int x, int y)
-    {
-        op.push_back((uint8_t)o);
-        a.push_back(x);
-        b.push_back(y);
-        return n_in + (int)op.size() - 1;
-    }
-    int wires() const { return n_in + (int)op.size(); }
-
-    void levelise()
-    {
-        std::vector<int32_t> wl(wires(), 0);
-        level.resize(op.size());
-        depth = 0;
-        for (size_t g = 0; g < op.size(); ++g) {
-            const int l = 1 + std::max(wl[a[g]], wl[b[g]]);
-            level[g] = l;
-            wl[n_in + g] = l;
-            depth = std::max(depth, l);
-        }
-    }
-};
 
 // Ripple-carry adder on wire vectors x, y (w bits); returns sum wires.
 static std::vector<int> build_add(Netlist &nl, const std::vector<int> &x, const std::vector<int> &y)
@@ -116,7 +87,7 @@ static std::vector<int> range_wires(int start, int count)
 
 // Input wires: ADD/MUL: A bits [0, w), B bits [w, 2w).  GATE: a = 0, b = 1.
 // MATVEC: M[r][c] bits at (r*cols + c)*w + bit, then v[c] bits.
-static bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
+bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
 {
     switch (kind) {
     case TFHE_CIRCUIT_GATE:
@@ -163,7 +134,7 @@ static bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
 }
 
 // Rows per instance of the two input groups.
-static void input_groups(int kind, int w, int rows, int cols, long &rows0, long &rows1)
+void input_groups(int kind, int w, int rows, int cols, long &rows0, long &rows1)
 {
     if (kind == TFHE_CIRCUIT_MATVEC) {
         rows0 = (long)rows * cols * w;
@@ -177,7 +148,7 @@ static void input_groups(int kind, int w, int rows, int cols, long &rows0, long 
 // Compiled plans
 // ---------------------------------------------------------------------
 
-__global__ void k_gather_rows(int32_t *dst, const int32_t *__restrict__ src,
+__global__ void k_gather_rows_impl(int32_t *dst, const int32_t *__restrict__ src,
                               const int32_t *__restrict__ rows, long count)
 {
     const long r = blockIdx.x;
@@ -187,6 +158,32 @@ __global__ void k_gather_rows(int32_t *dst, const int32_t *__restrict__ src,
     int4 *d = reinterpret_cast<int4 *>(dst + r * kLweStride);
     for (int k = threadIdx.x; k < kLweStride / 4; k += blockDim.x)
         d[k] = s[k];
+}
+
+cudaError_t launch_gather_rows(int32_t *dst, const int32_t *src, const int32_t *rows, long count,
+                               cudaStream_t st)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    k_gather_rows_impl<<<(unsigned)count, 128, 0, st>>>(dst, src, rows, count);
+    return cudaGetLastError();
+}
+
+std::shared_ptr<const Netlist> get_netlist(int kind, int w, int rows, int cols)
+{
+    static std::mutex mu;
+    static std::map<std::string, std::shared_ptr<const Netlist>> cache;
+    char key[64];
+    std::snprintf(key, sizeof(key), "%d:%d:%d:%d", kind, w, rows, cols);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end())
+        return it->second;
+    auto nl = std::make_shared<Netlist>();
+    if (!build_netlist(kind, w, rows, cols, *nl))
+        return nullptr;
+    cache.emplace(key, nl);
+    return nl;
 }
 
 struct JobLayout {
@@ -500,9 +497,7 @@ static int run_plan(tfhe_ctx *ctx, Plan &P, const tfhe_job *jobs, cudaStream_t s
         const long cnt = L.n_out * L.batch;
         if (cnt == 0)
             continue;
-        k_gather_rows<<<(unsigned)cnt, 128, 0, st>>>(jobs[j].out, P.pool, P.d_out_rows + L.out_off,
-                                                     cnt);
-        e = cudaGetLastError();
+        e = launch_gather_rows(jobs[j].out, P.pool, P.d_out_rows + L.out_off, cnt, st);
         ctx->launches += 1;
     }
     if (e != cudaSuccess)

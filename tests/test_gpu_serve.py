@@ -1,0 +1,125 @@
+"""Serving (continuous batching) through the C ABI: requests of mixed kinds
+and widths submitted while others run; every result is bit-identical to the
+same request run alone and to the oracle (n = 16 ring-size-1024 parameters
+so the oracle is quick), and a pool budget smaller than the mix forces
+requests to wait for rows without changing any result."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from conftest import oparams
+from paper_2005_01945_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    import torch
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    p = synth.TFHEParams(n=16)
+    P = oparams(p)
+    kd = synth.key_draws(p, 71)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    obk = orc.keygen_bk(P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+    oksk = orc.keygen_ksk(P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+    yield dict(torch=torch, api=api, p=p, P=P, kd=kd, bk=bk, ksk=ksk, obk=obk, oksk=oksk)
+
+
+def _requests(env, seed):
+    """A mix: (kind, width, rows, cols, dev in0, dev in1, host in0, host in1, out shape)."""
+    api, p, P, kd, orc = env["api"], env["p"], env["P"], env["kd"], __import__("oracle")
+    d = api.to_device
+    s_dev = d(kd.s)
+    rng = np.random.default_rng(seed)
+    kinds = [(api.GATE, api.XOR, 0, 0), (api.GATE, api.NAND, 0, 0), (api.ADD, 4, 0, 0),
+             (api.ADD, 8, 0, 0), (api.ADD, 16, 0, 0), (api.MUL, 4, 0, 0), (api.MUL, 6, 0, 0),
+             (api.MATVEC, 3, 2, 3)]
+    reqs = []
+    for k in range(24):
+        kind, w, r, c = kinds[rng.integers(len(kinds))]
+        if kind == api.MATVEC:
+            shp0, shp1, outshape = (r, c, w), (c, w), (r, w)
+        elif kind == api.GATE:
+            shp0, shp1, outshape = (1,), (1,), (1,)
+        else:
+            shp0, shp1, outshape = (w,), (w,), (w,)
+        bits = [synth.random_bits(shp, seed * 100 + k, f"in{j}") for j, shp in enumerate((shp0, shp1))]
+        cds = [synth.ct_draws(p, b.shape, seed * 100 + k, f"in{j}") for j, b in enumerate(bits)]
+        dev = [api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(b)) for cd, b in zip(cds, bits)]
+        host = [orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, b) for cd, b in zip(cds, bits)]
+        reqs.append((kind, w, r, c, dev[0], dev[1], host[0], host[1], outshape))
+    return reqs
+
+
+def _oracle(env, req):
+    orc, api = __import__("oracle"), env["api"]
+    kind, w, r, c, _, _, h0, h1, _ = req
+    P, bk, ksk = env["P"], env["obk"], env["oksk"]
+    if kind == api.GATE:
+        return orc.gates(P, bk, ksk, np.array([w], np.uint8), h0, h1)
+    if kind == api.ADD:
+        return orc.add(P, bk, ksk, w, h0[None], h1[None])[0][0]
+    if kind == api.MUL:
+        return orc.mul(P, bk, ksk, w, h0[None], h1[None])[0][0]
+    return orc.matvec(P, bk, ksk, w, h0, h1)[0]
+
+
+def _serve(env, reqs, budget, max_batch=0, spacing_s=0.0, threads=1):
+    torch, api, p = env["torch"], env["api"], env["p"]
+    ctx = api.Context(p)
+    ctx.set_keys(env["bk"], env["ksk"])
+    outs = [torch.zeros(req[8] + (api.LWE_STRIDE,), dtype=torch.int32, device="cuda") for req in reqs]
+    torch.cuda.synchronize()
+    ctx.serve_start(budget, max_batch)
+    ids = [None] * len(reqs)
+
+    def submit(part):
+        for k in part:
+            kind, w, r, c, d0, d1 = reqs[k][:6]
+            ids[k] = ctx.serve_submit(kind, w, d0, d1, outs[k], r, c)
+            if spacing_s:
+                time.sleep(spacing_s)
+
+    parts = [list(range(t, len(reqs), threads)) for t in range(threads)]
+    ths = [threading.Thread(target=submit, args=(pt,)) for pt in parts]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    lat = [ctx.serve_wait(i, 120000) for i in ids]
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    torch.cuda.synchronize()
+    res = [o.cpu().numpy().view(np.uint32)[..., :p.n + 1] for o in outs]
+    ctx.close()
+    return res, lat, stats
+
+
+def test_mix_equals_alone_and_oracle(env):
+    reqs = _requests(env, 5)
+    mixed, lat, stats = _serve(env, reqs, budget=256 << 20, spacing_s=0.002, threads=3)
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["iterations"] < sum(1 for _ in reqs) * 40   # levels were shared
+    assert all(x > 0 for x in lat)
+    for k, req in enumerate(reqs):
+        alone, _, _ = _serve(env, [req], budget=64 << 20)
+        assert np.array_equal(mixed[k], alone[0]), k
+        want = _oracle(env, req)
+        assert np.array_equal(mixed[k].reshape(want.shape), want), k
+
+
+def test_small_pool_forces_queueing(env):
+    """A pool that holds only a few requests at a time: requests wait for
+    rows (continuous admission) and every result is unchanged."""
+    reqs = _requests(env, 6)
+    roomy, _, _ = _serve(env, reqs, budget=256 << 20)
+    tight, _, stats = _serve(env, reqs, budget=400 * 2048, max_batch=64)
+    assert stats["completed"] == len(reqs)
+    for a, b in zip(roomy, tight):
+        assert np.array_equal(a, b)
