@@ -192,6 +192,21 @@ typedef struct {
 
 int tfhe_run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, void *stream);
 
+/* Level schedules of a job list (tfhe_run_jobs). */
+typedef enum {
+    TFHE_SCHED_ASAP = 0,     /* every gate at its earliest level              */
+    TFHE_SCHED_BALANCED = 1  /* default: deadline-driven list scheduling that  */
+                             /* fills each level up to a target width with the */
+                             /* ready gates of the earliest latest-start level */
+                             /* (same depth as ASAP; results identical)        */
+} tfhe_schedule;
+
+/* Host-only: the level widths of the schedule of `jobs` (pointers unused)
+ * under `policy` with target width `target` (0: 608); widths[0..cap) get the
+ * first cap levels.  Needs no context and no GPU. */
+int tfhe_schedule_info(const tfhe_job *jobs, size_t njobs, int policy, int64_t target,
+                       int32_t *widths, int32_t cap, int32_t *depth, int64_t *gates);
+
 /* Bootstrapped-gate count and depth (levels) of one instance of a circuit;
  * needs no context and no GPU. */
 int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, int32_t *depth);
@@ -203,8 +218,11 @@ typedef enum {
     TFHE_OPT_PROFILE = 2,    /* 1: record CUDA events around every blind-rotation   */
                              /*    and key-switch launch of circuit schedules (also */
                              /*    inside captured graphs)                          */
-    TFHE_OPT_BR_GROUP = 3    /* bootstraps per blind-rotation CTA: 1, 2 or 4, or 0  */
+    TFHE_OPT_BR_GROUP = 3,   /* bootstraps per blind-rotation CTA: 1, 2 or 4, or 0  */
                              /*    (default) to choose by batch size                */
+    TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
+    TFHE_OPT_LEVEL_WIDTH = 5 /* target gates per level for BALANCED (0: one wave,   */
+                             /*    4 bootstraps per SM)                             */
 } tfhe_option;
 
 int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);

@@ -65,6 +65,10 @@ EXPORTS = {
                     + [ctypes.c_void_p] * 4),
     "tfhe_run_jobs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "tfhe_schedule_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "tfhe_circuit_info": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int64),
                                                                ctypes.POINTER(ctypes.c_int32)]),
     "tfhe_ctx_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
@@ -94,7 +98,8 @@ EXPORTS = {
 }
 
 GATE, ADD, MUL, MATVEC = range(4)
-OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP = 0, 1, 2, 3
+OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH = range(6)
+SCHED_ASAP, SCHED_BALANCED = 0, 1
 
 
 class CJob(ctypes.Structure):
@@ -327,6 +332,22 @@ class Context:
 
     def serve_stop(self):
         self._c(lib().tfhe_serve_stop(self._h))
+
+
+def schedule_info(jobs, policy=1, target=0):
+    """Host-only level widths of a job list's schedule (no GPU needed).
+    jobs: list of (kind, width, rows, cols, batch).  -> (widths, gates)"""
+    arr = (CJob * len(jobs))()
+    for k, (kind, width, rows, cols, batch) in enumerate(jobs):
+        arr[k] = CJob(kind, width, rows, cols, batch, None, None, None)
+    depth, gates = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(lib().tfhe_schedule_info(arr, len(jobs), policy, target, None, 0,
+                                    ctypes.byref(depth), ctypes.byref(gates)))
+    widths = np.zeros(max(depth.value, 1), dtype=np.int32)
+    _check(lib().tfhe_schedule_info(arr, len(jobs), policy, target,
+                                    ctypes.c_void_p(widths.ctypes.data), depth.value,
+                                    ctypes.byref(depth), ctypes.byref(gates)))
+    return widths[:depth.value], int(gates.value)
 
 
 def circuit_info(kind, width, rows=0, cols=0):

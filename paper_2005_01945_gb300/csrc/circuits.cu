@@ -234,6 +234,8 @@ struct CircuitCache {
     bool use_graphs = true;
     bool per_gate = false;
     bool profile = false;
+    int policy = TFHE_SCHED_BALANCED;
+    long level_width = 0;            // 0: one wave (4 bootstraps per SM)
     std::vector<Plan *> profiled;    // plans whose events hold the last run
     cudaStream_t capture_stream = nullptr;
     ~CircuitCache()
@@ -269,18 +271,129 @@ static std::string signature(const tfhe_job *jobs, size_t njobs)
     return key;
 }
 
-static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, Plan &P)
+// Host-side schedule of a job list: pool layout, and every gate instance's
+// level.  No device memory is touched.
+struct Schedule {
+    std::vector<JobLayout> jobs;
+    long pool_rows = 0, gates = 0, max_width = 0, nout = 0;
+    int depth = 0;
+    std::vector<long> level_off;                 // depth + 1 entries
+    std::vector<uint8_t> ops;                    // per scheduled gate, level-major
+    std::vector<int32_t> ia, ib, io, outs;
+};
+
+// Deadline-driven list scheduling (policy TFHE_SCHED_BALANCED): gate g of a
+// netlist has ASAP level asap(g) and, for the schedule depth D, ALAP level
+// alap(g) = D + 1 - height(g), height = longest path to an output.  Level L
+// takes every ready gate whose deadline is L, then fills up to `target`
+// gates with the ready gates of the earliest deadlines.  By induction every
+// gate is ready by its deadline, so the depth stays D; widths exceed the
+// target only where the deadlines force it.  The ciphertexts do not depend
+// on the schedule (each gate is a deterministic function of its inputs).
+static void balanced_levels(const std::vector<const Netlist *> &nets, const std::vector<long> &batch,
+                            int D, long target, std::vector<std::vector<int32_t>> &level)
 {
-    std::vector<Netlist> nets(njobs);
+    const size_t nj = nets.size();
+    std::vector<std::vector<int32_t>> alap(nj), cons_off(nj), cons(nj);
+    std::vector<long> node_off(nj + 1, 0);
+    for (size_t j = 0; j < nj; ++j) {
+        const Netlist &nl = *nets[j];
+        const int G = (int)nl.op.size();
+        std::vector<int32_t> height(G, 1);
+        for (int g = G - 1; g >= 0; --g)
+            for (int in : {nl.a[g], nl.b[g]})
+                if (in >= nl.n_in)
+                    height[in - nl.n_in] = std::max(height[in - nl.n_in], height[g] + 1);
+        alap[j].resize(G);
+        for (int g = 0; g < G; ++g)
+            alap[j][g] = D + 1 - height[g];
+        cons_off[j].assign(G + 1, 0);
+        for (int g = 0; g < G; ++g)
+            for (int in : {nl.a[g], nl.b[g]})
+                if (in >= nl.n_in)
+                    cons_off[j][in - nl.n_in + 1]++;
+        for (int g = 0; g < G; ++g)
+            cons_off[j][g + 1] += cons_off[j][g];
+        cons[j].resize(cons_off[j][G]);
+        std::vector<int32_t> fillc(cons_off[j].begin(), cons_off[j].end() - 1);
+        for (int g = 0; g < G; ++g)
+            for (int in : {nl.a[g], nl.b[g]})
+                if (in >= nl.n_in)
+                    cons[j][fillc[in - nl.n_in]++] = g;
+        node_off[j + 1] = node_off[j] + batch[j] * G;
+        level[j].assign((size_t)batch[j] * G, 0);
+    }
+    const long total = node_off[nj];
+    std::vector<int32_t> pending(total);
+    // ready buckets by deadline; a node is (job, instance, gate) packed in node id
+    std::vector<std::vector<long>> bucket(D + 2);
+    std::vector<size_t> head(D + 2, 0);
+    auto job_of = [&](long node) {
+        return (size_t)(std::upper_bound(node_off.begin(), node_off.end(), node) - node_off.begin() - 1);
+    };
+    for (size_t j = 0; j < nj; ++j) {
+        const Netlist &nl = *nets[j];
+        const int G = (int)nl.op.size();
+        for (long inst = 0; inst < batch[j]; ++inst)
+            for (int g = 0; g < G; ++g) {
+                const long id = node_off[j] + inst * G + g;
+                pending[id] = (nl.a[g] >= nl.n_in) + (nl.b[g] >= nl.n_in);
+                if (pending[id] == 0)
+                    bucket[alap[j][g]].push_back(id);
+            }
+    }
+    long done = 0;
+    std::vector<long> chosen, fresh;
+    for (int L = 1; done < total; ++L) {
+        chosen.clear();
+        for (int a = 1; a <= D; ++a) {      // deadline L (and, defensively, earlier) first
+            if (a > L && (long)chosen.size() >= target)
+                break;
+            std::vector<long> &B = bucket[a];
+            while (head[a] < B.size() && (a <= L || (long)chosen.size() < target))
+                chosen.push_back(B[head[a]++]);
+        }
+        fresh.clear();
+        for (long id : chosen) {
+            const size_t j = job_of(id);
+            const Netlist &nl = *nets[j];
+            const long G = (long)nl.op.size(), rel = id - node_off[j];
+            const long inst = rel / G;
+            const int g = (int)(rel % G);
+            level[j][(size_t)rel] = L;
+            for (int q = cons_off[j][g]; q < cons_off[j][g + 1]; ++q) {
+                const long cid = node_off[j] + inst * G + cons[j][q];
+                if (--pending[cid] == 0)
+                    fresh.push_back(cid);
+            }
+        }
+        for (long id : fresh) {
+            const size_t j = job_of(id);
+            const long G = (long)nets[j]->op.size();
+            bucket[alap[j][(id - node_off[j]) % G]].push_back(id);
+        }
+        done += (long)chosen.size();
+    }
+}
+
+static int build_schedule(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int policy,
+                          long target, Schedule &S)
+{
+    std::vector<const Netlist *> nets(njobs);
+    std::vector<std::shared_ptr<const Netlist>> keep(njobs);
+    std::vector<long> batch(njobs);
     long pool = 0, nout = 0;
     int depth = 0;
     for (size_t j = 0; j < njobs; ++j) {
         const tfhe_job &J = jobs[j];
-        if (J.batch < 0 || (J.batch > 0 && (!J.in0 || !J.in1 || !J.out)))
-            return fail(ctx, TFHE_EINVAL, "job %zu: bad batch or null pointer", j);
-        if (!build_netlist(J.kind, J.width, J.rows, J.cols, nets[j]))
+        if (J.batch < 0)
+            return fail(ctx, TFHE_EINVAL, "job %zu: negative batch", j);
+        keep[j] = get_netlist(J.kind, J.width, J.rows, J.cols);
+        if (!keep[j])
             return fail(ctx, TFHE_EINVAL, "job %zu: unsupported circuit (kind %d width %d)", j,
                         J.kind, J.width);
+        nets[j] = keep[j].get();
+        batch[j] = J.batch;
         JobLayout L;
         L.kind = J.kind;
         L.w = J.width;
@@ -288,53 +401,92 @@ static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, Plan 
         L.cols = J.cols;
         L.batch = J.batch;
         L.base = pool;
-        L.inst_rows = nets[j].wires();
+        L.inst_rows = nets[j]->wires();
         input_groups(J.kind, J.width, J.rows, J.cols, L.rows0, L.rows1);
-        L.n_out = (long)nets[j].out.size();
+        L.n_out = (long)nets[j]->out.size();
         L.out_off = nout;
         pool += L.inst_rows * J.batch;
         nout += L.n_out * J.batch;
         if (J.batch > 0)
-            depth = std::max(depth, nets[j].depth);
-        P.jobs.push_back(L);
+            depth = std::max(depth, nets[j]->depth);
+        S.jobs.push_back(L);
     }
     if (pool >= (1L << 31) / 2)
         return fail(ctx, TFHE_EINVAL, "batch too large for one schedule (%ld pool rows)", pool);
-    // bucket gates by level
-    std::vector<long> count(depth + 2, 0);
-    for (size_t j = 0; j < njobs; ++j)
-        for (int l : nets[j].level)
-            count[l] += P.jobs[j].batch;
-    P.level_off.assign(depth + 1, 0);
-    for (int l = 1; l <= depth; ++l) {
-        P.level_off[l] = P.level_off[l - 1] + count[l];
-        P.max_width = std::max(P.max_width, count[l]);
-    }
-    // level l occupies [level_off[l-1], level_off[l])
-    const long total = P.level_off[depth];
-    std::vector<uint8_t> ops(total);
-    std::vector<int32_t> ia(total), ib(total), io(total), outs(nout);
-    std::vector<long> fill(P.level_off.begin(), P.level_off.end());
-    for (size_t j = 0; j < njobs; ++j) {
-        const Netlist &nl = nets[j];
-        const JobLayout &L = P.jobs[j];
-        for (long inst = 0; inst < L.batch; ++inst) {
-            const long b = L.base + inst * L.inst_rows;
-            for (size_t g = 0; g < nl.op.size(); ++g) {
-                const long k = fill[nl.level[g] - 1]++;
-                ops[k] = nl.op[g];
-                ia[k] = (int32_t)(b + nl.a[g]);
-                ib[k] = (int32_t)(b + nl.b[g]);
-                io[k] = (int32_t)(b + nl.n_in + (long)g);
-            }
-            for (size_t o = 0; o < nl.out.size(); ++o)
-                outs[L.out_off + inst * L.n_out + o] = (int32_t)(b + nl.out[o]);
+    // level of every gate instance
+    std::vector<std::vector<int32_t>> level(njobs);
+    if (policy == TFHE_SCHED_BALANCED && depth > 0) {
+        balanced_levels(nets, batch, depth, std::max(target, 1L), level);
+    } else {
+        for (size_t j = 0; j < njobs; ++j) {
+            level[j].resize((size_t)batch[j] * nets[j]->op.size());
+            for (long inst = 0; inst < batch[j]; ++inst)
+                std::copy(nets[j]->level.begin(), nets[j]->level.end(),
+                          level[j].begin() + inst * nets[j]->op.size());
         }
     }
-    P.pool_rows = pool;
-    P.gates = total;
-    P.depth = depth;
-    P.h_ops = ops;
+    int D = 0;
+    for (auto &lv : level)
+        for (int32_t l : lv)
+            D = std::max(D, (int)l);
+    std::vector<long> count(D + 2, 0);
+    for (auto &lv : level)
+        for (int32_t l : lv)
+            count[l]++;
+    S.level_off.assign(D + 1, 0);
+    for (int l = 1; l <= D; ++l) {
+        S.level_off[l] = S.level_off[l - 1] + count[l];
+        S.max_width = std::max(S.max_width, count[l]);
+    }
+    const long total = D ? S.level_off[D] : 0;
+    S.ops.resize(total);
+    S.ia.resize(total);
+    S.ib.resize(total);
+    S.io.resize(total);
+    S.outs.resize(nout);
+    std::vector<long> fill(S.level_off.begin(), S.level_off.end());
+    for (size_t j = 0; j < njobs; ++j) {
+        const Netlist &nl = *nets[j];
+        const JobLayout &L = S.jobs[j];
+        const long G = (long)nl.op.size();
+        for (long inst = 0; inst < L.batch; ++inst) {
+            const long b = L.base + inst * L.inst_rows;
+            for (long g = 0; g < G; ++g) {
+                const long k = fill[level[j][inst * G + g] - 1]++;
+                S.ops[k] = nl.op[g];
+                S.ia[k] = (int32_t)(b + nl.a[g]);
+                S.ib[k] = (int32_t)(b + nl.b[g]);
+                S.io[k] = (int32_t)(b + nl.n_in + g);
+            }
+            for (size_t o = 0; o < nl.out.size(); ++o)
+                S.outs[L.out_off + inst * L.n_out + o] = (int32_t)(b + nl.out[o]);
+        }
+    }
+    S.pool_rows = pool;
+    S.gates = total;
+    S.depth = D;
+    S.nout = nout;
+    return TFHE_OK;
+}
+
+static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int policy,
+                        long target, Plan &P)
+{
+    for (size_t j = 0; j < njobs; ++j)
+        if (jobs[j].batch > 0 && (!jobs[j].in0 || !jobs[j].in1 || !jobs[j].out))
+            return fail(ctx, TFHE_EINVAL, "job %zu: null pointer", j);
+    Schedule S;
+    int rc = build_schedule(ctx, jobs, njobs, policy, target, S);
+    if (rc != TFHE_OK)
+        return rc;
+    P.jobs = S.jobs;
+    P.pool_rows = S.pool_rows;
+    P.gates = S.gates;
+    P.max_width = S.max_width;
+    P.depth = S.depth;
+    P.level_off = S.level_off;
+    P.h_ops = S.ops;
+    const long total = S.gates, nout = S.nout, pool = S.pool_rows;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **p, size_t bytes) {
         if (e == cudaSuccess && bytes)
@@ -348,16 +500,16 @@ static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, Plan 
     alloc((void **)&P.d_io, std::max(total, 1L) * sizeof(int32_t));
     alloc((void **)&P.d_out_rows, std::max(nout, 1L) * sizeof(int32_t));
     if (e == cudaSuccess && total) {
-        e = cudaMemcpy(P.d_ops, ops.data(), total, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(P.d_ops, S.ops.data(), total, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(P.d_ia, ia.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(P.d_ia, S.ia.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(P.d_ib, ib.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(P.d_ib, S.ib.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(P.d_io, io.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(P.d_io, S.io.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && nout)
-        e = cudaMemcpy(P.d_out_rows, outs.data(), nout * sizeof(int32_t), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(P.d_out_rows, S.outs.data(), nout * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "compile schedule");
     return TFHE_OK;
@@ -512,11 +664,13 @@ int run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, cudaStream_t st)
     if (njobs == 0)
         return TFHE_OK;
     CircuitCache &C = cache_of(ctx);
-    const std::string key = signature(jobs, njobs);
+    const long target = C.level_width > 0 ? C.level_width : 4L * ctx->num_sms;
+    const std::string key = signature(jobs, njobs) + "|" + std::to_string(C.policy) + ":" +
+                            std::to_string(target);
     auto it = C.plans.find(key);
     if (it == C.plans.end()) {
         std::unique_ptr<Plan> P(new Plan());
-        int rc = compile_plan(ctx, jobs, njobs, *P);
+        int rc = compile_plan(ctx, jobs, njobs, C.policy, target, *P);
         if (rc != TFHE_OK)
             return rc;
         if (C.order.size() >= 32) {   // keep device memory bounded
@@ -583,6 +737,25 @@ int tfhe_matvec(tfhe_ctx *ctx, int width, int rows, int cols, const int32_t *M, 
     return one_job(ctx, TFHE_CIRCUIT_MATVEC, width, rows, cols, M, v, y, 1, stream);
 }
 
+int tfhe_schedule_info(const tfhe_job *jobs, size_t njobs, int policy, int64_t target,
+                       int32_t *widths, int32_t cap, int32_t *depth, int64_t *gates)
+{
+    if ((njobs && !jobs) || target < 0)
+        return TFHE_EINVAL;
+    Schedule S;
+    int rc = build_schedule(nullptr, jobs, njobs, policy, target > 0 ? (long)target : 608L, S);
+    if (rc != TFHE_OK)
+        return rc;
+    if (depth)
+        *depth = S.depth;
+    if (gates)
+        *gates = S.gates;
+    if (widths)
+        for (int l = 1; l <= S.depth && l <= cap; ++l)
+            widths[l - 1] = (int32_t)(S.level_off[l] - S.level_off[l - 1]);
+    return TFHE_OK;
+}
+
 int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, int32_t *depth)
 {
     Netlist nl;
@@ -609,6 +782,16 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
         return TFHE_OK;
     case TFHE_OPT_PROFILE:
         C.profile = value != 0;
+        return TFHE_OK;
+    case TFHE_OPT_SCHEDULE:
+        if (value != TFHE_SCHED_ASAP && value != TFHE_SCHED_BALANCED)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_SCHEDULE must be ASAP or BALANCED");
+        C.policy = (int)value;
+        return TFHE_OK;
+    case TFHE_OPT_LEVEL_WIDTH:
+        if (value < 0)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_LEVEL_WIDTH must be >= 0");
+        C.level_width = (long)value;
         return TFHE_OK;
     case TFHE_OPT_BR_GROUP:
         if (value != 0 && value != 1 && value != 2 && value != 4)

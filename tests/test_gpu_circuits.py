@@ -132,9 +132,14 @@ def test_mixed_jobs_and_schedules_agree(small):
         else:
             E.ctx.set_option(api.OPT_GRAPHS, mode != "nograph")
             E.ctx.set_option(api.OPT_PER_GATE, mode == "pergate")
+            E.ctx.set_option(api.OPT_SCHEDULE, api.SCHED_ASAP if mode == "asap" else
+                             api.SCHED_BALANCED)
+            E.ctx.set_option(api.OPT_LEVEL_WIDTH, 7 if mode == "narrow" else 0)
             E.ctx.run_jobs(jobs)
             E.ctx.set_option(api.OPT_GRAPHS, 1)
             E.ctx.set_option(api.OPT_PER_GATE, 0)
+            E.ctx.set_option(api.OPT_SCHEDULE, api.SCHED_BALANCED)
+            E.ctx.set_option(api.OPT_LEVEL_WIDTH, 0)
         return [E.host(o) for o in outs]
 
     mixed = run("graph")
@@ -144,7 +149,7 @@ def test_mixed_jobs_and_schedules_agree(small):
     assert np.array_equal(mixed[0], want_add)
     assert np.array_equal(mixed[1], want_mul)
     assert np.array_equal(mixed[2][:, 0], want_xor)
-    for mode in ("alone", "nograph", "pergate"):
+    for mode in ("alone", "nograph", "pergate", "asap", "narrow"):
         other = run(mode)
         for x, y in zip(mixed, other):
             assert np.array_equal(x, y), mode

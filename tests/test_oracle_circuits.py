@@ -124,3 +124,21 @@ def test_library_netlists_match_count_table():
     for (kind, w, r, c), g in _counts().items():
         assert api.circuit_info(kinds[kind], w, r, c)[0] == g
     assert api.circuit_info(api.ADD, 32)[1] == 62
+
+
+def test_balanced_schedule_invariants():
+    """Host-only schedules: the deadline-driven list schedule keeps the ASAP
+    depth, covers every gate once, and keeps levels at the target width
+    wherever deadlines allow (for the 256 x add32 batch: all but the last)."""
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    for jobs in ([(api.ADD, 32, 0, 0, 256)], [(api.MUL, 16, 0, 0, 64), (api.MUL, 32, 0, 0, 64)],
+                 [(api.MATVEC, 8, 4, 5, 2)], [(api.GATE, api.XOR, 0, 0, 100)]):
+        wa, ga = api.schedule_info(jobs, api.SCHED_ASAP, 608)
+        wb, gb = api.schedule_info(jobs, api.SCHED_BALANCED, 608)
+        assert ga == gb == sum(k[4] * api.circuit_info(k[0], k[1], k[2], k[3])[0] for k in jobs)
+        assert wa.sum() == wb.sum() == ga
+        assert len(wb) == len(wa)
+        assert wb.min() > 0
+    wb, _ = api.schedule_info([(api.ADD, 32, 0, 0, 256)], api.SCHED_BALANCED, 608)
+    assert (wb[:-1] == 608).all() and wb[-1] == 39424 - 61 * 608
