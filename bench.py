@@ -376,6 +376,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    tuned = ctx.autotune()
     ctx.set_option(api.OPT_PROFILE, 1)
     for _ in range(args.warmup):
         ctx.add_n(WIDTH, A, B, R)
@@ -514,6 +515,8 @@ def main():
                 "config": {"workload": WORKLOAD, "gates_per_step": gates_step, "batch": BATCH,
                            "width": WIDTH, "levels": 62,
                            "l2": "flushed between timed steps (256 MB write)",
+                           "schedule": "deadline-balanced levels, one wave (4 bootstraps/SM)",
+                           "autotuned": tuned,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "mul32_latency": latency, "verified": verified}

@@ -227,6 +227,17 @@ typedef enum {
 
 int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);
 
+/* Autotune the launch shapes of the two bootstrapping kernels for this
+ * context's device: for each level-width bucket (<= 152, 304, 608, 1216,
+ * 2432, 4864, 9728 gates, and more) time 1, 2 and 4 bootstraps per
+ * blind-rotation CTA and 1..32 key-switch j-chunks on synthetic
+ * ciphertexts, and keep the fastest (a few seconds; results never change).
+ * cache_path (may be NULL): a text file consulted first and appended to
+ * after tuning, keyed by device name and SM count.  choices (may be NULL)
+ * receives 16 ints: the 8 blind-rotation group sizes, then the 8 key-switch
+ * chunk counts.  Synchronous. */
+int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t *choices);
+
 /* Kernel launches the context has issued so far (kernels inside a replayed
  * graph count once per replay). */
 int tfhe_ctx_launches(const tfhe_ctx *ctx, uint64_t *launches);

@@ -72,6 +72,7 @@ EXPORTS = {
     "tfhe_circuit_info": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int64),
                                                                ctypes.POINTER(ctypes.c_int32)]),
     "tfhe_ctx_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "tfhe_ctx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]),
     "tfhe_ctx_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "tfhe_ctx_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64),
@@ -277,6 +278,16 @@ class Context:
 
     def set_option(self, option, value):
         self._c(lib().tfhe_ctx_set_option(self._h, option, int(value)))
+
+    def autotune(self, cache_path=None) -> dict:
+        """Pick blind-rotation group sizes and key-switch j-splits per level
+        width by timing them on this device (results are unchanged)."""
+        ch = np.zeros(16, dtype=np.int32)
+        self._c(lib().tfhe_ctx_autotune(self._h, cache_path.encode() if cache_path else None,
+                                        ctypes.c_void_p(ch.ctypes.data)))
+        edges = ["<=152", "<=304", "<=608", "<=1216", "<=2432", "<=4864", "<=9728", ">9728"]
+        return {"br_group": dict(zip(edges, ch[:8].tolist())),
+                "ks_chunks": dict(zip(edges, ch[8:].tolist()))}
 
     def launches(self) -> int:
         v = ctypes.c_uint64(0)

@@ -38,12 +38,17 @@
 
 namespace tgb {
 
+// Shared-memory slots of 33 x 32 words: a transpose written as
+// slot[i * 33 + lane] and read as slot[lane * 33 + j] is conflict-free with
+// register + immediate addresses (no per-element address arithmetic).
+constexpr int kSlot = 33 * 32;
+
 struct NttConst {
     uint32_t za[2][32][2];   // forward stage A: w64^brv5(k), Shoup companion
     uint32_t zd[2][32][2];   // forward stage D: cyclic size-32 twiddles
     uint32_t iza[2][32][2];  // inverse of stage A
     uint32_t izd[2][32][2];  // inverse of stage D
-    uint32_t qneg_inv[2];    // -q^-1 mod 2^32
+    uint32_t q_inv[2];       // q^-1 mod 2^32
     uint32_t crt_c, crt_cp;  // q0^-1 mod q1 and its Shoup companion mod q1
     uint32_t p_lo, pad;      // (q0 q1) mod 2^32
     uint64_t p_half;         // (q0 q1 + 1) / 2
@@ -123,7 +128,7 @@ __device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 // Forward negacyclic NTT of one polynomial held by one warp.
 // In : lane l, register r holds coefficient l + 32 r, value in [0, 2q).
 // Out: lane l, register r holds the evaluation at psi^(2 (l + 32 brv5(r)) + 1),
-//      value in [0, 4q).  sbuf: 1024 words of this warp's shared memory.
+//      value in [0, 4q).  sbuf: kSlot words of this warp's shared memory.
 __device__ __forceinline__ void fwd_ntt(uint32_t (&x)[32], uint32_t *sbuf, int lane,
                                         const uint2 *__restrict__ twb, const Prime &pr)
 {
@@ -134,15 +139,14 @@ __device__ __forceinline__ void fwd_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
         const uint2 t = __ldg(tw + r * 32);
         x[r] = mul_shoup(x[r], t.x, t.y, pr.q);
     }
+    uint32_t *wr = sbuf + lane, *rd = sbuf + lane * 33;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const int k1 = brv5(r);
-        sbuf[k1 * 32 + (lane ^ k1)] = x[r];
-    }
+    for (int r = 0; r < 32; ++r)
+        wr[brv5(r) * 33] = x[r];       // lane i1, k1 = brv5(r) -> slot[k1][i1]
     __syncwarp();
 #pragma unroll
     for (int i1 = 0; i1 < 32; ++i1)
-        x[i1] = sbuf[lane * 32 + (i1 ^ lane)];
+        x[i1] = rd[i1];                // lane k1 reads slot[k1][i1]
     __syncwarp();
     ct32<true>(x, pr);
 }
@@ -160,13 +164,14 @@ __device__ __forceinline__ void inv_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
         const uint2 t = __ldg(tw + r * 32);
         x[r] = mul_shoup(x[r], t.x, t.y, pr.q);
     }
+    uint32_t *wr = sbuf + lane_brv, *rd = sbuf + lane * 33;
 #pragma unroll
     for (int r = 0; r < 32; ++r)
-        sbuf[r * 32 + (lane_brv ^ r)] = x[r];
+        wr[r * 33] = x[r];             // lane k1, i1 = r -> slot[i1][brv5(k1)]
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < 32; ++r)
-        x[r] = sbuf[lane * 32 + (r ^ lane)];
+        x[r] = rd[r];                  // lane i1 reads slot[i1][r]
     __syncwarp();
     gs32<false>(x, pr);
 }
@@ -180,7 +185,7 @@ __device__ __forceinline__ void inv_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
 __global__ void __launch_bounds__(128) k_bk_to_ntt(const int32_t *__restrict__ bk, uint32_t *out,
                                                    int n, const uint2 *__restrict__ twb)
 {
-    __shared__ uint32_t sbuf[4][1024];
+    __shared__ uint32_t sbuf[4][kSlot];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long task = (long)blockIdx.x * 4 + warp;  // ((i * 4 + r) * 2 + p) * 2 + q
     if (task >= (long)n * kRows * 2 * 2)
@@ -226,7 +231,7 @@ struct BrArgs {
 
 struct BrSmem {                 // one bootstrap
     uint32_t acc[2][kN];        // TLWE accumulator (a(X), b(X))
-    uint32_t fwd[4][2][kN];     // forward outputs [digit][prime][reg*32+lane]
+    uint32_t fwd[4][2][kSlot];  // forward outputs [digit][prime][reg*32+lane]; transpose scratch
     uint16_t abar[kLweStride];  // mod-switched mask and body
 };
 
@@ -272,7 +277,7 @@ __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
                                              const uint4 *__restrict__ bkp, int lane,
                                              const Prime &pr)
 {
-    const uint32_t qn = c_ntt.qneg_inv[pr.P];
+    const uint32_t qn = c_ntt.q_inv[pr.P];
     const uint32_t *f0 = S.fwd[0][pr.P], *f1 = S.fwd[1][pr.P], *f2 = S.fwd[2][pr.P],
                    *f3 = S.fwd[3][pr.P];
 #pragma unroll
@@ -302,22 +307,22 @@ __device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4,
 
 // Phase 4: CRT of (r0 mod q0, r1 mod q1) to the centred integer, mod 2^32,
 // added into the accumulator.  Warp (p, h) does registers 16h .. 16h + 15.
-// Garner: u = (r1 - r0) q0^-1 mod q1, v = r0 + q0 u in [0, q0 q1); v is
-// centred (v - q0 q1) when v >= (q0 q1 + 1)/2, which for r0 < q0 holds iff
-// u > (q1 - 1)/2, or u = (q1 - 1)/2 and r0 >= (q0 + 1)/2.
+// Garner: u = (r1 - r0) q0^-1 mod q1, v = r0 + q0 u in [0, q0 q1).  The
+// exact coefficient S satisfies |S| <= 4 N 2^9 2^31 = 2^52, so for S >= 0
+// u = floor(S / q0) < 2^25, and for S < 0 (v = S + q0 q1) u > q1 - 2^25:
+// the centring decision (v >= q0 q1 / 2) is exactly u > (q1 - 1) / 2.
 __device__ __forceinline__ void br_crt(BrSmem &S, int p, int h, int lane)
 {
     const uint32_t *x0 = S.fwd[p * 2 + 0][1], *x1 = S.fwd[p * 2 + 1][1];
     const uint32_t c = c_ntt.crt_c, cp = c_ntt.crt_cp, plo = c_ntt.p_lo;
-    constexpr uint32_t uh = (kQ1 - 1) / 2, rh = (kQ0 + 1) / 2;
+    constexpr uint32_t uh = (kQ1 - 1) / 2;
     uint32_t *acc = S.acc[p];
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
         const int e = (16 * h + rr) * 32 + lane;
         const uint32_t r0 = x0[e], r1 = x1[e];
         const uint32_t u = csub(mul_shoup(r1 - r0 + 2 * kQ1, c, cp, kQ1), kQ1);
-        const bool neg = u > uh || (u == uh && r0 >= rh);
-        acc[e] += r0 + kQ0 * u - (neg ? plo : 0u);
+        acc[e] += r0 + kQ0 * u - (u > uh ? plo : 0u);
     }
 }
 
@@ -511,11 +516,11 @@ cudaError_t upload_ntt_constants(uint2 *twb_dev, cudaStream_t stream)
                 twb[((P * 2 + 0) * 32 + r) * 32 + l] = make_uint2(f, shoup_of(f, q));
                 twb[((P * 2 + 1) * 32 + r) * 32 + l] = make_uint2(iv, shoup_of(iv, q));
             }
-        // -q^-1 mod 2^32 by Newton iteration
+        // q^-1 mod 2^32 by Newton iteration
         uint32_t inv = q;
         for (int it = 0; it < 5; ++it)
             inv *= 2u - q * inv;
-        C.qneg_inv[P] = 0u - inv;
+        C.q_inv[P] = inv;
         const uint64_t ninv = powmod(kN, q - 2, q);
         const uint32_t sc = (uint32_t)mulmod((((uint64_t)1 << 32) % q), ninv, q);
         C.bk_scale[P][0] = sc;
@@ -585,10 +590,13 @@ int br_blocks_per_sm()
 
 // Lockstep group size: several bootstraps per CTA share instruction fetch
 // and key reads, but leave SMs idle when a level is narrow.
-static int br_group(long count, int num_sms, int forced)
+static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 {
     if (forced == 1 || forced == 2 || forced == 4)
         return forced;
+    const int t = tuned[tune_bucket(count)];
+    if (t == 1 || t == 2 || t == 4)
+        return t;
     const long per_sm = (count + num_sms - 1) / num_sms;
     return per_sm >= 8 ? 4 : (per_sm >= 3 ? 2 : 1);
 }
@@ -617,7 +625,7 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     cudaGetDevice(&dev);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int B = br_group(count, sms > 0 ? sms : 1, keys.br_group);
+    const int B = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
     const long groups = (count + B - 1) / B;
     long blocks_per_sm = B == 4 ? br_blocks<4>(dev) : (B == 2 ? br_blocks<2>(dev) : br_blocks<1>(dev));
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);

@@ -253,6 +253,17 @@ static CircuitCache &cache_of(tfhe_ctx *ctx)
     return *ctx->circuits;
 }
 
+void invalidate_graphs(tfhe_ctx *ctx)
+{
+    if (!ctx->circuits)
+        return;
+    for (auto &kv : ctx->circuits->plans)
+        if (kv.second->graph) {
+            cudaGraphExecDestroy(kv.second->graph);
+            kv.second->graph = nullptr;
+        }
+}
+
 void release_circuits(tfhe_ctx *ctx)
 {
     delete ctx->circuits;
@@ -549,12 +560,12 @@ static cudaError_t enqueue_levels(tfhe_ctx *ctx, Plan &P, cudaStream_t st, bool 
             e = mark(3 * (l - 1) + 1);
         if (e == cudaSuccess)
             e = launch_keyswitch(ctx->keys.ksk, P.big, P.pool, P.d_io + off, P.pool_rows, cnt,
-                                 ctx->prm.n, ctx->num_sms, ctx->status, st);
+                                 ctx->prm.n, ctx->num_sms, ctx->status, st, ctx->keys.tune_ks);
         if (e == cudaSuccess)
             e = mark(3 * (l - 1) + 2);
         if (e != cudaSuccess)
             return e;
-        kernels += 1 + keyswitch_kernels(cnt, ctx->num_sms);
+        kernels += 1 + keyswitch_kernels(cnt, ctx->num_sms, ctx->keys.tune_ks);
     }
     P.kernels_per_run = kernels;
     return cudaSuccess;
@@ -570,10 +581,10 @@ static cudaError_t enqueue_per_gate(tfhe_ctx *ctx, Plan &P, cudaStream_t st)
         if (e != cudaSuccess)
             return e;
         e = launch_keyswitch(ctx->keys.ksk, P.big, P.pool, P.d_io + k, P.pool_rows, 1, ctx->prm.n,
-                             ctx->num_sms, ctx->status, st);
+                             ctx->num_sms, ctx->status, st, ctx->keys.tune_ks);
         if (e != cudaSuccess)
             return e;
-        ctx->launches += 1 + keyswitch_kernels(1, ctx->num_sms);
+        ctx->launches += 1 + keyswitch_kernels(1, ctx->num_sms, ctx->keys.tune_ks);
     }
     return cudaSuccess;
 }
@@ -797,11 +808,7 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
         if (value != 0 && value != 1 && value != 2 && value != 4)
             return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2 or 4");
         ctx->keys.br_group = (int)value;
-        for (auto &kv : C.plans)   // captured graphs hold the old launch shape
-            if (kv.second->graph) {
-                cudaGraphExecDestroy(kv.second->graph);
-                kv.second->graph = nullptr;
-            }
+        invalidate_graphs(ctx);   // captured graphs hold the old launch shape
         return TFHE_OK;
     default:
         return fail(ctx, TFHE_EINVAL, "unknown option %d", option);
@@ -835,7 +842,7 @@ int tfhe_ctx_profile(tfhe_ctx *ctx, double *br_ms, int64_t *br_launches, int64_t
             kt += b;
             bl += 1;
             bb += cnt;
-            kl += keyswitch_kernels(cnt, ctx->num_sms);
+            kl += keyswitch_kernels(cnt, ctx->num_sms, ctx->keys.tune_ks);
         }
     }
     C.profiled.clear();

@@ -54,13 +54,14 @@ __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m)
     return min(x, x - m);
 }
 
-// Montgomery reduction of a 64-bit x < q 2^32: returns x 2^-32 mod q in
-// [0, 2q).  qneg_inv = -q^-1 mod 2^32.
-__device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t qneg_inv)
+// Montgomery reduction of a 64-bit x = hi 2^32 + lo < q 2^32: with
+// m = lo q^-1 mod 2^32, m q has low word lo, so x - m q = (hi - mulhi(m, q))
+// 2^32 exactly; the result hi - mulhi(m, q) + q = x 2^-32 mod q lies in
+// (0, 2q).  q_inv = q^-1 mod 2^32.
+__device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t q_inv)
 {
-    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-    uint32_t m = lo * qneg_inv;
-    return hi + __umulhi(m, q) + (lo != 0u ? 1u : 0u);
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return hi - __umulhi(lo * q_inv, q) + q;
 }
 #endif  // __CUDACC__
 
@@ -71,6 +72,20 @@ struct DevKeys {
     const uint2 *twb;      // stage-B twiddles [2 prime][2 dir][32 reg][32 lane] (w, w')
     int n;
     int br_group;          // bootstraps per blind-rotation CTA: 1, 2, 4, or 0 = by batch size
+    // Autotuned launch shapes per level-width bucket (0 = not tuned): bucket b
+    // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
+    int8_t tune_br[8];     // bootstraps per blind-rotation CTA
+    int8_t tune_ks[8];     // key-switch j-chunks
 };
+
+constexpr long kTuneEdge[8] = {152, 304, 608, 1216, 2432, 4864, 9728, 1L << 40};
+
+inline int tune_bucket(long count)
+{
+    int b = 0;
+    while (b < 7 && count > kTuneEdge[b])
+        ++b;
+    return b;
+}
 
 }  // namespace tgb

@@ -137,8 +137,16 @@ __global__ void __launch_bounds__(kKsThreads) k_keyswitch(const KsArgs A)
     }
 }
 
-static int ks_chunks(long count, int num_sms)
+static int ks_forced_chunks = 0;   // set while the autotuner measures
+
+// j-chunks: the tuned value for the width bucket, else enough CTAs for two
+// per SM.
+static int ks_chunks(long count, int num_sms, const int8_t *tuned)
 {
+    if (ks_forced_chunks)
+        return ks_forced_chunks;
+    if (tuned && tuned[tune_bucket(count)] > 0)
+        return tuned[tune_bucket(count)];
     const long tiles = (count + kKsGates - 1) / kKsGates;
     int chunks = 1;
     while (chunks < 32 && tiles * chunks < 2L * num_sms)
@@ -146,21 +154,24 @@ static int ks_chunks(long count, int num_sms)
     return chunks;
 }
 
+void keyswitch_force_chunks(int chunks) { ks_forced_chunks = chunks; }
+
 // Kernels one launch_keyswitch call issues.
-int keyswitch_kernels(long count, int num_sms)
+int keyswitch_kernels(long count, int num_sms, const int8_t *tuned)
 {
-    return count <= 0 ? 0 : (ks_chunks(count, num_sms) > 1 ? 2 : 1);
+    return count <= 0 ? 0 : (ks_chunks(count, num_sms, tuned) > 1 ? 2 : 1);
 }
 
 // Splits the j-range so that small batches still occupy the GPU.
 cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
                              const int32_t *idx_out, long rows_out, long count, int n,
-                             int num_sms, uint32_t *status, cudaStream_t stream)
+                             int num_sms, uint32_t *status, cudaStream_t stream,
+                             const int8_t *tuned)
 {
     if (count <= 0)
         return cudaSuccess;
     const long tiles = (count + kKsGates - 1) / kKsGates;
-    const int chunks = ks_chunks(count, num_sms);
+    const int chunks = ks_chunks(count, num_sms, tuned);
     KsArgs A;
     A.ksk = ksk;
     A.big = big;

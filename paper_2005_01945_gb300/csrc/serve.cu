@@ -329,7 +329,8 @@ static void srv_loop(Server *Sp)
                                     ctx->br_grid, S.st);
         if (e == cudaSuccess)
             e = launch_keyswitch(ctx->keys.ksk, S.big, S.pool, I.d_idx + 2 * icap, S.pool_rows,
-                                 count, ctx->prm.n, ctx->num_sms, ctx->status, S.st);
+                                 count, ctx->prm.n, ctx->num_sms, ctx->status, S.st,
+                                 ctx->keys.tune_ks);
         o = 0;
         for (SrvReq *r : finishing) {
             const long no = (long)r->nl->out.size();
@@ -348,7 +349,8 @@ static void srv_loop(Server *Sp)
         I.gates = count;
         {
             std::lock_guard<std::mutex> lock(S.mu);
-            ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms) + (long)finishing.size();
+            ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms, ctx->keys.tune_ks) +
+                             (long)finishing.size();
             S.stats.gates += count;
             S.stats.iterations++;
             for (SrvReq *r : take)

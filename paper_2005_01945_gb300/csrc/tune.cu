@@ -1,0 +1,194 @@
+// tune.cu -- autotuner for the launch shapes of the two bootstrapping
+// kernels: bootstraps per blind-rotation CTA (1, 2 or 4 in lockstep) and the
+// key switch's j-split (1 .. 32 chunks), chosen per level-width bucket by
+// timing the candidates on synthetic ciphertexts with the context's keys.
+// Results can be cached in a small text file keyed by device name and SM
+// count.  Launch shapes never change results (the arithmetic is exact and
+// order-independent), only time.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "runtime.h"
+
+namespace tgb {
+
+// Deterministic pseudo-random ciphertext words (splitmix-style hash), so the
+// tuned kernels see realistic mod-switched masks.
+__global__ void k_fill_random(int32_t *p, long words, uint64_t seed)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < words;
+         i += (long)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        p[i] = (int32_t)(uint32_t)(z >> 32);
+    }
+}
+
+static std::string cache_key(int device)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return "unknown";
+    }
+    std::string name = prop.name;
+    for (char &c : name)
+        if (c == ' ')
+            c = '_';
+    return name + ":" + std::to_string(prop.multiProcessorCount);
+}
+
+static bool load_cache(const char *path, const std::string &key, DevKeys &k)
+{
+    FILE *f = path ? std::fopen(path, "r") : nullptr;
+    if (!f)
+        return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char kbuf[256];
+        int br[8], ks[8];
+        if (std::sscanf(line, "%255s br %d %d %d %d %d %d %d %d ks %d %d %d %d %d %d %d %d", kbuf,
+                        &br[0], &br[1], &br[2], &br[3], &br[4], &br[5], &br[6], &br[7], &ks[0],
+                        &ks[1], &ks[2], &ks[3], &ks[4], &ks[5], &ks[6], &ks[7]) == 17 &&
+            key == kbuf) {
+            for (int b = 0; b < 8; ++b) {
+                k.tune_br[b] = (int8_t)br[b];
+                k.tune_ks[b] = (int8_t)ks[b];
+            }
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void save_cache(const char *path, const std::string &key, const DevKeys &k)
+{
+    FILE *f = path ? std::fopen(path, "a") : nullptr;
+    if (!f)
+        return;
+    std::fprintf(f, "%s br", key.c_str());
+    for (int b = 0; b < 8; ++b)
+        std::fprintf(f, " %d", k.tune_br[b]);
+    std::fprintf(f, " ks");
+    for (int b = 0; b < 8; ++b)
+        std::fprintf(f, " %d", k.tune_ks[b]);
+    std::fprintf(f, "\n");
+    std::fclose(f);
+}
+
+}  // namespace tgb
+
+using namespace tgb;
+
+extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t *choices)
+{
+    if (!ctx)
+        return TFHE_EINVAL;
+    if (!ctx->keys_loaded)
+        return fail(ctx, TFHE_EINVAL, "tfhe_ctx_autotune: keys not set");
+    DeviceGuard dg(ctx->device);
+    const std::string key = cache_key(ctx->device);
+    DevKeys &K = ctx->keys;
+    if (!load_cache(cache_path, key, K)) {
+        const long widths[8] = {152, 304, 608, 1216, 2432, 4864, 9728, 16384};
+        const long maxw = widths[7];
+        int32_t *cts = nullptr, *big = nullptr, *out = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaStream_t st = nullptr;
+        cudaError_t e = cudaMalloc(&cts, maxw * kLweStride * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&big, maxw * kBigStride * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&out, maxw * kLweStride * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&e0);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) {
+            k_fill_random<<<1024, 256, 0, st>>>(cts, maxw * kLweStride, 0x2005);
+            e = cudaGetLastError();
+        }
+        const int saved_group = K.br_group;
+        int8_t br[8] = {0}, ks[8] = {0};
+        for (int b = 0; b < 8 && e == cudaSuccess; ++b) {
+            const long W = widths[b];
+            float best = 1e30f;
+            for (int B : {1, 2, 4}) {
+                K.br_group = B;
+                float tot = 0;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess)
+                        e = launch_blind_rotate(K, nullptr, cts, nullptr, W, nullptr, nullptr, 0,
+                                                big, W, kMu, ctx->status, ctx->br_grid, st);
+                    if (e == cudaSuccess)
+                        e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess)
+                        e = cudaEventSynchronize(e1);
+                    float ms = 0;
+                    if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                        tot += ms;   // first run is a warm-up
+                }
+                if (e == cudaSuccess && tot < best) {
+                    best = tot;
+                    br[b] = (int8_t)B;
+                }
+            }
+            best = 1e30f;
+            for (int c : {1, 2, 4, 8, 16, 32}) {
+                if ((W + 15) / 16 * c > 64L * ctx->num_sms)   // far more CTAs than useful
+                    continue;
+                keyswitch_force_chunks(c);
+                float tot = 0;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess)
+                        e = launch_keyswitch(K.ksk, big, out, nullptr, W, W, ctx->prm.n,
+                                             ctx->num_sms, ctx->status, st);
+                    if (e == cudaSuccess)
+                        e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess)
+                        e = cudaEventSynchronize(e1);
+                    float ms = 0;
+                    if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                        tot += ms;
+                }
+                keyswitch_force_chunks(0);
+                if (e == cudaSuccess && tot < best) {
+                    best = tot;
+                    ks[b] = (int8_t)c;
+                }
+            }
+        }
+        K.br_group = saved_group;
+        keyswitch_force_chunks(0);
+        cudaFree(cts);
+        cudaFree(big);
+        cudaFree(out);
+        if (e0)
+            cudaEventDestroy(e0);
+        if (e1)
+            cudaEventDestroy(e1);
+        if (st)
+            cudaStreamDestroy(st);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "tfhe_ctx_autotune");
+        std::memcpy(K.tune_br, br, sizeof(br));
+        std::memcpy(K.tune_ks, ks, sizeof(ks));
+        save_cache(cache_path, key, K);
+        // captured graphs hold launch shapes chosen before tuning
+        invalidate_graphs(ctx);
+    }
+    if (choices)
+        for (int b = 0; b < 8; ++b) {
+            choices[b] = K.tune_br[b];
+            choices[8 + b] = K.tune_ks[b];
+        }
+    return TFHE_OK;
+}

@@ -195,3 +195,22 @@ def test_each_lockstep_group_bit_exact(gpu, orc, group):
         gpu["ctx"].set_option(api.OPT_BR_GROUP, 0)
     want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
     assert np.array_equal(_u32(out)[:, :p.n + 1], want)
+
+
+def test_autotune_keeps_results(gpu, orc):
+    """Autotuning changes launch shapes only: outputs before and after are
+    identical (and equal to the oracle)."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    count = 21
+    bits, cts, dev = _fresh(gpu, orc, count, 77, "tune")
+    ops = ((np.arange(count) * 7) % 6).astype(np.uint8)
+    before = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    after = torch.zeros_like(before)
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], before)
+    choices = gpu["ctx"].autotune()
+    assert set(choices["br_group"].values()) <= {1, 2, 4}
+    assert set(choices["ks_chunks"].values()) <= {1, 2, 4, 8, 16, 32}
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], after)
+    assert torch.equal(before, after)
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
+    assert np.array_equal(_u32(after)[:, :p.n + 1], want)
