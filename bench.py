@@ -48,6 +48,21 @@ OPS_PER_CMUX = 12 * 5120 * 7 + 12 * 1024 * 3 + 4 * 1024 * 12 + 4 * 1024 * 8 + 2 
 INT32_LANES_PER_SM = 128
 
 
+def max_over_ranks(value, dist, device=None):
+    """Largest value over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step, steps, world, max_ms):
+    """Units all ranks processed divided by the slowest rank's time (s)."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,12 +421,8 @@ def main():
     barrier()
     launches = ctx.launches() - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = gates_step * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = whole_job_rate(gates_step, args.steps, world, total_ms)
 
     # ---- correctness of the timed result (decryption on the device)
     dec = api.decrypt_bits(p, s_dev, R).cpu().numpy()
@@ -437,12 +448,8 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": gates_step * args.steps * world / (e2e_total / 1e3), "unit": "gates/s",
+    e2e_total = max_over_ranks(sum(e2e_ms), dist, dev)
+    e2e = {"value": whole_job_rate(gates_step, args.steps, world, e2e_total), "unit": "gates/s",
            "h2d_bytes_per_step": A.numel() * 4 + B.numel() * 4,
            "d2h_bytes_per_step": R.numel() * 4}
 
