@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson requests at 3 rates (config 4)")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--configs", action="store_true",
+                    help="time configs 0 (8 gates), 2 (mul16/mul32 x64) and 3 (matvec 16x16)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (read if present, appended after tuning)")
     return ap.parse_args()
 
 
@@ -235,6 +239,82 @@ def run_br_only(count, group=0):
     ctx.close()
 
 
+def run_configs(args):
+    """Throughput of the other workloads (device-resident inputs, CUDA events,
+    L2 flushed before every timed run), each verified by decryption."""
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    seed = synth.MASTER_SEED
+    kd = synth.key_draws(p, seed)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    ctx.autotune(args.tune_cache)
+    s_dev = d(kd.s)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def enc(xs, w, tag):
+        bits = synth.to_bits(xs, w)
+        cd = synth.ct_draws(p, bits.shape, seed, tag)
+        return api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(bits))
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    dec = lambda t: synth.from_bits(api.decrypt_bits(p, s_dev, t).cpu().numpy())  # noqa: E731
+    out = {}
+    # config 0: 8 gates
+    ops, ba, bb = synth.gates8_inputs(seed)
+    A0, B0 = enc(ba, 1, "c0a")[:, 0], enc(bb, 1, "c0b")[:, 0]
+    R0 = torch.empty_like(A0)
+    ops_d = d(ops)
+    ms = timed(lambda: ctx.bootstrap_gates(ops_d, A0, B0, R0), 10)
+    out["config0_8gates"] = {"ms": ms, "gates_per_s": 8 / (ms / 1e3)}
+    # config 2: 64 mul16 + 64 mul32 in one schedule
+    a16, b16 = synth.int_pairs(64, 16, seed + 2, "mul16")
+    a32, b32 = synth.int_pairs(64, 32, seed + 2, "mul32")
+    A16, B16, A32, B32 = enc(a16, 16, "m16a"), enc(b16, 16, "m16b"), enc(a32, 32, "m32a"), \
+        enc(b32, 32, "m32b")
+    R16, R32 = torch.empty_like(A16), torch.empty_like(A32)
+    jobs = [dict(kind=api.MUL, width=16, batch=64, in0=A16, in1=B16, out=R16),
+            dict(kind=api.MUL, width=32, batch=64, in0=A32, in1=B32, out=R32)]
+    ms = timed(lambda: ctx.run_jobs(jobs), 3)
+    gates = 64 * (api.circuit_info(api.MUL, 16)[0] + api.circuit_info(api.MUL, 32)[0])
+    ok = bool(np.array_equal(dec(R16), (a16 * b16) % (1 << 16)) and
+              np.array_equal(dec(R32), (a32 * b32) % (1 << 32)))
+    out["config2_mul16x64_mul32x64"] = {"ms": ms, "gates": gates,
+                                        "gates_per_s": gates / (ms / 1e3), "verified": ok}
+    # config 3: matvec 16x16, 16-bit
+    M = synth.random_uints((16, 16), 16, seed + 3, "M")
+    v = synth.random_uints(16, 16, seed + 3, "v")
+    MM, vv = enc(M, 16, "M"), enc(v, 16, "v")
+    y = torch.empty((16, 16, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+    ms = timed(lambda: ctx.matvec(16, MM, vv, y), 3)
+    gates = api.circuit_info(api.MATVEC, 16, 16, 16)[0]
+    ok = bool(np.array_equal(dec(y), (M * v[None, :]).sum(axis=1) % (1 << 16)))
+    out["config3_matvec16"] = {"ms": ms, "gates": gates, "gates_per_s": gates / (ms / 1e3),
+                               "verified": ok}
+    print(json.dumps({"metric": "bootstrapped gates/sec per workload", "unit": "gates/s",
+                      "results": out}), flush=True)
+    ctx.close()
+
+
 SERVE_KINDS = [("gate", 0, 1), ("add16", 1, 16), ("add32", 1, 32), ("mul16", 2, 16),
                ("mul32", 2, 32)]
 
@@ -352,6 +432,9 @@ def main():
     if args.serve:
         run_serve(args)
         return
+    if args.configs:
+        run_configs(args)
+        return
     import torch
     from paper_2005_01945_gb300 import api, build, synth
 
@@ -391,7 +474,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    tuned = ctx.autotune()
+    tuned = ctx.autotune(args.tune_cache)
     ctx.set_option(api.OPT_PROFILE, 1)
     for _ in range(args.warmup):
         ctx.add_n(WIDTH, A, B, R)
