@@ -78,11 +78,43 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson requests at 3 rates (config 4)")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--variants", action="store_true",
+                    help="adder / multiplier variants and the compound-gate ablation")
     ap.add_argument("--configs", action="store_true",
                     help="time configs 0 (8 gates), 2 (mul16/mul32 x64) and 3 (matvec 16x16)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (read if present, appended after tuning)")
     return ap.parse_args()
+
+
+KERNEL_SOURCES = ("paper_2005_01945_gb300/csrc/bootstrap.cu",
+                  "paper_2005_01945_gb300/csrc/common.cuh")
+TRAFFIC_PROFILE = "profiles/k_blind_rotate_traffic_add32x256.md"
+
+
+def kernel_source_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def br_traffic_per_launch():
+    """DRAM bytes per blind-rotation launch from the committed ncu capture,
+    or None when the kernel sources changed since it was taken."""
+    try:
+        fields = {}
+        for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
+            if ":" in line and line.strip().startswith(("bytes_per_launch", "kernel_source_sha1")):
+                k, v = line.strip().split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_source_sha1") != kernel_source_sha1():
+            return None
+        return float(fields["bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def measured_peaks():
@@ -236,6 +268,94 @@ def run_br_only(count, group=0):
         ks.append(e1.elapsed_time(e2))
     print(json.dumps({"br_only": count, "group": group, "br_ms": br, "ks_ms": ks,
                       "bootstraps_per_s": count / (min(br) / 1e3)}), flush=True)
+    ctx.close()
+
+
+def run_variants(args):
+    """Circuit variants of the paper (sections V-A, V-B): adders (ripple carry,
+    majority carry, number-wise GPU_n) and multipliers (sequential, tree
+    accumulation), as batches and as single-request latency; and the
+    compound-gate ablation (section V-A-3, Fig. "compoundGateAna"): the XOR
+    and AND of two w-bit numbers as two launches or as one."""
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    seed = synth.MASTER_SEED + 5
+    kd = synth.key_draws(p, seed)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    ctx.autotune(args.tune_cache)
+    s_dev = d(kd.s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def enc(xs, w, tag):
+        bits = synth.to_bits(xs, w)
+        cd = synth.ct_draws(p, bits.shape, seed, tag)
+        return api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(bits))
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    dec = lambda t: synth.from_bits(api.decrypt_bits(p, s_dev, t).cpu().numpy())  # noqa: E731
+    res = {"adders_256x32": {}, "multipliers_32": {}, "compound_gate": []}
+    a, b = synth.int_pairs(256, 32, seed, "var_add")
+    A, B = enc(a, 32, "va"), enc(b, 32, "vb")
+    R = torch.empty_like(A)
+    for name, kind in (("ripple", api.ADD), ("majority", api.ADD_MAJ), ("numberwise", api.ADD_NW)):
+        job = [dict(kind=kind, width=32, batch=256, in0=A, in1=B, out=R)]
+        ms = timed(lambda: ctx.run_jobs(job), 3)
+        g, depth = api.circuit_info(kind, 32)
+        res["adders_256x32"][name] = {"ms": ms, "gates": 256 * g, "depth": depth,
+                                      "gates_per_s": 256 * g / (ms / 1e3),
+                                      "verified": bool(np.array_equal(dec(R), (a + b) % (1 << 32)))}
+        one = [dict(kind=kind, width=32, batch=1, in0=A[:1], in1=B[:1], out=R[:1])]
+        res["adders_256x32"][name]["single_ms"] = timed(lambda: ctx.run_jobs(one), 5)
+    ma, mb = synth.int_pairs(64, 32, seed, "var_mul")
+    MA, MB = enc(ma, 32, "vma"), enc(mb, 32, "vmb")
+    MR = torch.empty_like(MA)
+    for name, kind in (("sequential", api.MUL), ("tree", api.MUL_TREE)):
+        job = [dict(kind=kind, width=32, batch=64, in0=MA, in1=MB, out=MR)]
+        ms = timed(lambda: ctx.run_jobs(job), 2)
+        g, depth = api.circuit_info(kind, 32)
+        ok = bool(np.array_equal(dec(MR), (ma * mb) % (1 << 32)))
+        one = [dict(kind=kind, width=32, batch=1, in0=MA[:1], in1=MB[:1], out=MR[:1])]
+        res["multipliers_32"][name] = {"batch64_ms": ms, "gates": 64 * g, "depth": depth,
+                                       "gates_per_s": 64 * g / (ms / 1e3),
+                                       "single_ms": timed(lambda: ctx.run_jobs(one), 5),
+                                       "verified": ok}
+    for w in (1, 2, 4, 8, 16, 32):
+        x, y = synth.int_pairs(1, w, seed, f"cg{w}")
+        X, Y = enc(x, w, f"cgx{w}")[0], enc(y, w, f"cgy{w}")[0]
+        out = torch.empty((2 * w, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+        xor_ops = d(np.full(w, api.XOR, np.uint8))
+        and_ops = d(np.full(w, api.AND, np.uint8))
+        both = d(np.array([api.XOR] * w + [api.AND] * w, np.uint8))
+        XX, YY = torch.cat([X, X]), torch.cat([Y, Y])
+
+        def two():
+            ctx.bootstrap_gates(xor_ops, X, Y, out[:w])
+            ctx.bootstrap_gates(and_ops, X, Y, out[w:])
+
+        def one():
+            ctx.bootstrap_gates(both, XX, YY, out)
+
+        res["compound_gate"].append({"bits": w, "two_launches_ms": timed(two, 5),
+                                     "one_launch_ms": timed(one, 5)})
+    print(json.dumps({"metric": "circuit variants (sections V-A, V-B)", "results": res}),
+          flush=True)
     ctx.close()
 
 
@@ -435,6 +555,9 @@ def main():
     if args.configs:
         run_configs(args)
         return
+    if args.variants:
+        run_variants(args)
+        return
     import torch
     from paper_2005_01945_gb300 import api, build, synth
 
@@ -548,7 +671,9 @@ def main():
                 "peak": peak_ops / 1e12, "unit": "Tops/s (int32)", "frac": achieved / peak_ops,
                 "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} INT32 "
                               f"lanes x {sm_max:.0f} MHz (max SM clock)",
-                "traffic": None, "launches": br_launch, "avg_launch_ms": br_ms / max(br_launch, 1),
+                "traffic": br_traffic_per_launch(), "traffic_unit": "bytes per launch (ncu dram)",
+                "algorithmic_bytes_per_launch": 32.8e6 + br_boot / max(br_launch, 1) * 8192,
+                "launches": br_launch, "avg_launch_ms": br_ms / max(br_launch, 1),
                 "share_of_step": br_ms / max(sum(step_ms), 1e-9),
                 "keyswitch_share_of_step": ks_ms / max(sum(step_ms), 1e-9)}
 

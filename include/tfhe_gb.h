@@ -67,11 +67,17 @@ typedef enum {
     TFHE_EDEVICE = -6   /* a kernel reported an error in the status word */
 } tfhe_status;
 
-/* Gate opcodes.  Gate g computes c = (0, mu_g) + alpha_g * (ca + cb) and
- * bootstraps it:  NAND (+1/8, -1), AND (-1/8, +1), OR (+1/8, +1),
- * XOR (+1/4, +2), NOR (-1/8, -1), XNOR (-1/4, -2). */
+/* Gate opcodes.  Gate g computes c = (0, mu_g) + alpha_a ca + alpha_b cb
+ * (+ alpha_c cc) and bootstraps it; (mu, alpha_a, alpha_b, alpha_c):
+ *   NAND (+1/8, -1, -1), AND (-1/8, +1, +1), OR (+1/8, +1, +1),
+ *   XOR (+1/4, +2, +2), NOR (-1/8, -1, -1), XNOR (-1/4, -2, -2),
+ *   ANDNY = AND(NOT a, b) (-1/8, -1, +1), ANDYN = AND(a, NOT b) (-1/8, +1, -1),
+ *   ORNY = OR(NOT a, b) (+1/8, -1, +1), ORYN = OR(a, NOT b) (+1/8, +1, -1),
+ *   MAJ = majority of three (0, +1, +1, +1): the only 3-input gate; it is
+ *   available in circuits (a third input wire), not in tfhe_bootstrap_gates. */
 typedef enum {
-    TFHE_NAND = 0, TFHE_AND = 1, TFHE_OR = 2, TFHE_XOR = 3, TFHE_NOR = 4, TFHE_XNOR = 5
+    TFHE_NAND = 0, TFHE_AND = 1, TFHE_OR = 2, TFHE_XOR = 3, TFHE_NOR = 4, TFHE_XNOR = 5,
+    TFHE_MAJ = 6, TFHE_ANDNY = 7, TFHE_ANDYN = 8, TFHE_ORNY = 9, TFHE_ORYN = 10
 } tfhe_gate;
 
 /* ------------------------------------------------------------------ */
@@ -101,7 +107,8 @@ int tfhe_last_error(const tfhe_ctx *ctx, char *buf, size_t len);
 /* Read and clear the device status word (synchronises the context's
  * device).  Returns TFHE_OK or TFHE_EDEVICE; *code (may be NULL) receives
  * the raw word: bit 0 gather index out of range, bit 1 scatter index out of
- * range, bit 2 bounded wait timed out. */
+ * range, bit 2 bounded wait timed out, bit 3 opcode without its inputs
+ * (MAJ given no third input, or an unknown opcode). */
 int tfhe_ctx_status(tfhe_ctx *ctx, uint32_t *code);
 
 /* ------------------------------------------------------------------ */
@@ -174,10 +181,17 @@ int tfhe_matvec(tfhe_ctx *ctx, int width, int rows, int cols, const int32_t *M,
  * batch) is compiled once and cached; its level sequence is replayed as a
  * CUDA graph. */
 typedef enum {
-    TFHE_CIRCUIT_GATE = 0,   /* one gate, opcode in `width`          */
-    TFHE_CIRCUIT_ADD = 1,    /* tfhe_add_n                           */
-    TFHE_CIRCUIT_MUL = 2,    /* tfhe_mul_n                           */
-    TFHE_CIRCUIT_MATVEC = 3  /* tfhe_matvec (rows x cols)            */
+    TFHE_CIRCUIT_GATE = 0,     /* one 2-input gate, opcode in `width`             */
+    TFHE_CIRCUIT_ADD = 1,      /* tfhe_add_n: ripple carry, 5w - 6 gates, depth 2w-2 */
+    TFHE_CIRCUIT_MUL = 2,      /* tfhe_mul_n: sequential shift-and-add           */
+    TFHE_CIRCUIT_MATVEC = 3,   /* tfhe_matvec (rows x cols)                      */
+    TFHE_CIRCUIT_ADD_MAJ = 4,  /* ripple adder with majority carries:            */
+                               /*   3w - 2 gates, depth w (one MAJ per carry)     */
+    TFHE_CIRCUIT_ADD_NW = 5,   /* the paper's number-wise adder GPU_n (section    */
+                               /*   V-B-1): w rounds of (R AND B, R XOR B, B<<1),  */
+                               /*   w^2 gates, depth w                            */
+    TFHE_CIRCUIT_MUL_TREE = 6  /* multiplication with tree-based accumulation    */
+                               /*   of the partial products (section V-B-2)       */
 } tfhe_circuit;
 
 typedef struct {

@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "libtfhe_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NAND, AND, OR, XOR, NOR, XNOR = range(6)
+NAND, AND, OR, XOR, NOR, XNOR, MAJ, ANDNY, ANDYN, ORNY, ORYN = range(11)
 MU = 1 << 29  # 1/8 on the torus
 
 
@@ -75,6 +75,11 @@ def lib():
             "orc_keygen_bk": (None, [P, vp, vp, vp, vp, vp]),
             "orc_keygen_ksk": (None, [P, vp, vp, vp, vp, vp]),
             "orc_gate_combine": (None, [i32, i32, vp, vp, vp]),
+            "orc_gate_combine3": (None, [i32, i32, vp, vp, vp, vp]),
+            "orc_gate3": (None, [P, vp, vp, i32, vp, vp, vp, vp]),
+            "orc_add_maj": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_add_nw": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_mul_tree": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_blind_rotate_many": (None, [P, vp, i64, vp, u32, vp, i32]),
             "orc_sample_extract": (None, [i32, vp, vp]),
             "orc_keyswitch_many": (None, [P, vp, i64, vp, vp]),
@@ -242,6 +247,44 @@ def add(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
     R = np.empty_like(A)
     g = lib().orc_add(ctypes.byref(P), _p(bk), _p(ksk), w, batch, _p(A), _p(B), _p(R), nthreads)
     return R, int(g)
+
+
+def _circuit(name, P, bk, ksk, w, A, B, nthreads):
+    bk, ksk, A, B = _u32(bk), _u32(ksk), _u32(A), _u32(B)
+    batch = A.size // (w * (P.n + 1))
+    R = np.empty_like(A)
+    g = getattr(lib(), name)(ctypes.byref(P), _p(bk), _p(ksk), w, batch, _p(A), _p(B), _p(R),
+                             nthreads)
+    return R, int(g)
+
+
+def add_maj(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Ripple adder with majority-gate carries -> (R, gates)."""
+    return _circuit("orc_add_maj", P, bk, ksk, w, A, B, nthreads)
+
+
+def add_nw(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """The paper's number-wise adder GPU_n -> (R, gates)."""
+    return _circuit("orc_add_nw", P, bk, ksk, w, A, B, nthreads)
+
+
+def mul_tree(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Multiplication with tree-based accumulation -> (R, gates)."""
+    return _circuit("orc_mul_tree", P, bk, ksk, w, A, B, nthreads)
+
+
+def gate3(P: Params, bk, ksk, op: int, ca, cb, cc) -> np.ndarray:
+    ca, cb, cc, bk, ksk = _u32(ca), _u32(cb), _u32(cc), _u32(bk), _u32(ksk)
+    out = np.empty_like(ca)
+    lib().orc_gate3(ctypes.byref(P), _p(bk), _p(ksk), int(op), _p(ca), _p(cb), _p(cc), _p(out))
+    return out
+
+
+def gate_combine3(P: Params, op: int, ca, cb, cc) -> np.ndarray:
+    ca, cb, cc = _u32(ca), _u32(cb), _u32(cc)
+    out = np.empty_like(ca)
+    lib().orc_gate_combine3(P.n, int(op), _p(ca), _p(cb), _p(cc), _p(out))
+    return out
 
 
 def mul(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):

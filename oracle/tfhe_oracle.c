@@ -48,8 +48,10 @@ typedef struct {
     int32_t ks_basebit; /* log2 of the key-switch base                    */
 } orc_params;
 
-/* Gate opcodes (the boolean gates the paper evaluates, section II-A). */
-enum { ORC_NAND = 0, ORC_AND = 1, ORC_OR = 2, ORC_XOR = 3, ORC_NOR = 4, ORC_XNOR = 5 };
+/* Gate opcodes (the boolean gates the paper evaluates, section II-A, and
+ * the negated-input and majority gates of TFHE's gate set). */
+enum { ORC_NAND = 0, ORC_AND = 1, ORC_OR = 2, ORC_XOR = 3, ORC_NOR = 4, ORC_XNOR = 5,
+       ORC_MAJ = 6, ORC_ANDNY = 7, ORC_ANDYN = 8, ORC_ORNY = 9, ORC_ORYN = 10 };
 
 #define ORC_MU (UINT32_C(1) << 29) /* 1/8 on the torus */
 
@@ -242,23 +244,46 @@ void orc_keygen_ksk(const orc_params *P, const int32_t *s, const int32_t *S,
 /* ------------------------------------------------------------------ */
 
 /* Linear part of a bootstrapped gate under the encoding bit 1 -> +1/8,
- * bit 0 -> -1/8: c = (0, mu_g) + alpha * (ca + cb).  The sign of the phase of
- * c is the gate's truth value before the bootstrap re-encrypts it. */
+ * bit 0 -> -1/8: c = (0, mu_g) + alpha_a ca + alpha_b cb (+ cc for MAJ).
+ * The sign of the phase of c is the gate's truth value before the
+ * bootstrap re-encrypts it: e.g. AND has phase -1/8 + a + b, positive only
+ * for a = b = +1/8; a negated input enters with the opposite sign (NOT x
+ * has phase -x); MAJ sums three +-1/8 phases, positive iff two or three
+ * inputs are 1. */
+static void gate_linear(int32_t op, uint32_t *mu, int32_t *alpha_a, int32_t *alpha_b)
+{
+    switch (op) {
+    case ORC_NAND:  *mu = ORC_MU;                   *alpha_a = -1; *alpha_b = -1; break;
+    case ORC_AND:   *mu = (uint32_t)0 - ORC_MU;     *alpha_a = 1;  *alpha_b = 1;  break;
+    case ORC_OR:    *mu = ORC_MU;                   *alpha_a = 1;  *alpha_b = 1;  break;
+    case ORC_XOR:   *mu = 2 * ORC_MU;               *alpha_a = 2;  *alpha_b = 2;  break;
+    case ORC_NOR:   *mu = (uint32_t)0 - ORC_MU;     *alpha_a = -1; *alpha_b = -1; break;
+    case ORC_XNOR:  *mu = (uint32_t)0 - 2 * ORC_MU; *alpha_a = -2; *alpha_b = -2; break;
+    case ORC_MAJ:   *mu = 0;                        *alpha_a = 1;  *alpha_b = 1;  break;
+    case ORC_ANDNY: *mu = (uint32_t)0 - ORC_MU;     *alpha_a = -1; *alpha_b = 1;  break;
+    case ORC_ANDYN: *mu = (uint32_t)0 - ORC_MU;     *alpha_a = 1;  *alpha_b = -1; break;
+    case ORC_ORNY:  *mu = ORC_MU;                   *alpha_a = -1; *alpha_b = 1;  break;
+    default:        *mu = ORC_MU;                   *alpha_a = 1;  *alpha_b = -1; break; /* ORYN */
+    }
+}
+
 void orc_gate_combine(int32_t n, int32_t op, const uint32_t *ca, const uint32_t *cb, uint32_t *out)
 {
     uint32_t mu;
-    int32_t alpha;
-    switch (op) {
-    case ORC_NAND: mu = ORC_MU;                     alpha = -1; break;
-    case ORC_AND:  mu = (uint32_t)0 - ORC_MU;       alpha = 1;  break;
-    case ORC_OR:   mu = ORC_MU;                     alpha = 1;  break;
-    case ORC_XOR:  mu = 2 * ORC_MU;                 alpha = 2;  break;
-    case ORC_NOR:  mu = (uint32_t)0 - ORC_MU;       alpha = -1; break;
-    default:       mu = (uint32_t)0 - 2 * ORC_MU;   alpha = -2; break; /* XNOR */
-    }
+    int32_t aa, ab;
+    gate_linear(op, &mu, &aa, &ab);
     for (int32_t i = 0; i <= n; i++)
-        out[i] = (uint32_t)alpha * (ca[i] + cb[i]);
+        out[i] = (uint32_t)aa * ca[i] + (uint32_t)ab * cb[i];
     out[n] += mu;
+}
+
+/* Three-input combine: MAJ(a, b, c) has linear part ca + cb + cc. */
+void orc_gate_combine3(int32_t n, int32_t op, const uint32_t *ca, const uint32_t *cb,
+                       const uint32_t *cc, uint32_t *out)
+{
+    orc_gate_combine(n, op, ca, cb, out);
+    for (int32_t i = 0; i <= n; i++)
+        out[i] += cc[i];
 }
 
 /* Blind rotation.  abar[0..n-1] are the mod-switched mask words, abar[n] the
@@ -369,6 +394,16 @@ void orc_gate(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int3
 {
     uint32_t *c = malloc(sizeof(uint32_t) * (P->n + 1));
     orc_gate_combine(P->n, op, ca, cb, c);
+    orc_bootstrap(P, bk, ksk, c, ORC_MU, out);
+    free(c);
+}
+
+/* One bootstrapped 3-input gate (MAJ). */
+void orc_gate3(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t op,
+               const uint32_t *ca, const uint32_t *cb, const uint32_t *cc, uint32_t *out)
+{
+    uint32_t *c = malloc(sizeof(uint32_t) * (P->n + 1));
+    orc_gate_combine3(P->n, op, ca, cb, cc, c);
     orc_bootstrap(P, bk, ksk, c, ORC_MU, out);
     free(c);
 }
@@ -523,6 +558,182 @@ static void ev_matvec_row(orc_ev *E, int32_t w, int32_t cols, const uint32_t *Mr
     free(terms); free(next);
 }
 
+/* Wires that may be the constant 0 (NULL).  Every gate output gets a fresh
+ * buffer from the arena, freed when the circuit is done. */
+typedef struct {
+    uint32_t **buf;
+    int64_t n, cap, words;
+} orc_arena;
+
+static uint32_t *arena_new(orc_arena *A)
+{
+    if (A->n == A->cap) {
+        A->cap = A->cap ? 2 * A->cap : 64;
+        A->buf = realloc(A->buf, sizeof(uint32_t *) * A->cap);
+    }
+    return A->buf[A->n++] = malloc(sizeof(uint32_t) * A->words);
+}
+
+static void arena_free(orc_arena *A)
+{
+    for (int64_t i = 0; i < A->n; i++)
+        free(A->buf[i]);
+    free(A->buf);
+}
+
+/* One adder position with operands x, y and incoming carry c, any of which
+ * may be the constant 0 (NULL).  Only the live operands are combined: one
+ * live operand is the sum itself; two give a half adder (sum XOR, carry
+ * AND); three give a full adder -- sum (x XOR y) XOR c, and carry either
+ * (x AND y) OR ((x XOR y) AND c) (Eq. "addcarry") or MAJ(x, y, c).  The
+ * carry is formed only when need_carry is set. */
+static void ev_cell(orc_ev *E, orc_arena *A, const uint32_t *x, const uint32_t *y,
+                    const uint32_t *c, int need_carry, int maj, const uint32_t **sum,
+                    const uint32_t **carry)
+{
+    const uint32_t *live[3];
+    int k = 0;
+    if (x) live[k++] = x;
+    if (y) live[k++] = y;
+    if (c) live[k++] = c;
+    *sum = NULL;
+    *carry = NULL;
+    if (k == 1) {
+        *sum = live[0];
+    } else if (k == 2) {
+        uint32_t *s = arena_new(A);
+        ev_gate(E, ORC_XOR, live[0], live[1], s);
+        *sum = s;
+        if (need_carry) {
+            uint32_t *co = arena_new(A);
+            ev_gate(E, ORC_AND, live[0], live[1], co);
+            *carry = co;
+        }
+    } else if (k == 3) {
+        uint32_t *p = arena_new(A), *s = arena_new(A);
+        ev_gate(E, ORC_XOR, x, y, p);
+        ev_gate(E, ORC_XOR, p, c, s);
+        *sum = s;
+        if (need_carry) {
+            uint32_t *co = arena_new(A);
+            if (maj) {
+                orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, x, y, c, co);
+                E->gates++;
+            } else {
+                uint32_t *g = arena_new(A), *t = arena_new(A);
+                ev_gate(E, ORC_AND, x, y, g);
+                ev_gate(E, ORC_AND, p, c, t);
+                ev_gate(E, ORC_OR, g, t, co);
+            }
+            *carry = co;
+        }
+    }
+}
+
+/* w-bit sum mod 2^w of wire vectors with constant-zero entries. */
+static void ev_add_cells(orc_ev *E, orc_arena *A, int32_t w, const uint32_t **x,
+                         const uint32_t **y, int maj, const uint32_t **r)
+{
+    const uint32_t *c = NULL;
+    for (int32_t i = 0; i < w; i++)
+        ev_cell(E, A, x[i], y[i], c, i < w - 1, maj, &r[i], &c);
+}
+
+static void copy_out(int32_t w, int64_t W, const uint32_t **r, uint32_t *R)
+{
+    for (int32_t i = 0; i < w; i++)
+        memcpy(R + i * W, r[i], sizeof(uint32_t) * W);
+}
+
+/* Ripple adder whose carries are single majority gates. */
+static void ev_add_maj(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    orc_arena A = {NULL, 0, 0, W};
+    const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
+                   **r = malloc(sizeof(*r) * w);
+    for (int32_t i = 0; i < w; i++) {
+        x[i] = Av + i * W;
+        y[i] = Bv + i * W;
+    }
+    ev_add_cells(E, &A, w, x, y, 1, r);
+    copy_out(w, W, r, R);
+    free(x); free(y); free(r);
+    arena_free(&A);
+}
+
+/* The paper's number-wise addition GPU_n (section V-B-1): R = A; then w
+ * times C = R AND B, R = R XOR B, B = C << 1, on every bit at once.  Bits of
+ * B that are the constant 0 (shifted in) leave R unchanged and give no
+ * carry; the carry out of the top bit is dropped. */
+static void ev_add_nw(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    orc_arena A = {NULL, 0, 0, W};
+    const uint32_t **r = malloc(sizeof(*r) * w), **b = malloc(sizeof(*b) * w),
+                   **nb = malloc(sizeof(*nb) * w);
+    for (int32_t i = 0; i < w; i++) {
+        r[i] = Av + i * W;
+        b[i] = Bv + i * W;
+    }
+    for (int32_t k = 0; k < w; k++) {
+        for (int32_t i = 0; i < w; i++)
+            nb[i] = NULL;
+        for (int32_t i = 0; i < w; i++) {
+            if (!b[i])
+                continue;
+            uint32_t *nr = arena_new(&A);
+            if (i + 1 < w) {
+                uint32_t *cy = arena_new(&A);
+                ev_gate(E, ORC_AND, r[i], b[i], cy);
+                nb[i + 1] = cy;
+            }
+            ev_gate(E, ORC_XOR, r[i], b[i], nr);
+            r[i] = nr;
+        }
+        for (int32_t i = 0; i < w; i++)
+            b[i] = nb[i];
+    }
+    copy_out(w, W, r, R);
+    free(r); free(b); free(nb);
+    arena_free(&A);
+}
+
+/* Truncated multiplication with tree-based accumulation (section V-B-2):
+ * partial product i is A AND b_i shifted left by i (its low i bits the
+ * constant 0); the w partial products are added pairwise, (0,1), (2,3),
+ * ..., an odd last one moving up unchanged, until one is left. */
+static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    orc_arena A = {NULL, 0, 0, W};
+    const uint32_t **terms = malloc(sizeof(*terms) * w * w), **next = malloc(sizeof(*next) * w * w);
+    for (int32_t i = 0; i < w; i++)
+        for (int32_t j = 0; j < w; j++) {
+            uint32_t *pp = NULL;
+            if (j >= i) {
+                pp = arena_new(&A);
+                ev_gate(E, ORC_AND, Av + (j - i) * W, Bv + i * W, pp);
+            }
+            terms[i * w + j] = pp;
+        }
+    int32_t cnt = w;
+    while (cnt > 1) {
+        int32_t k = 0;
+        for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
+            ev_add_cells(E, &A, w, terms + i * w, terms + (i + 1) * w, 0, next + k * w);
+        if (cnt & 1) {
+            memcpy(next + k * w, terms + (cnt - 1) * w, sizeof(*terms) * w);
+            k++;
+        }
+        memcpy(terms, next, sizeof(*terms) * w * k);
+        cnt = k;
+    }
+    copy_out(w, W, terms, R);
+    free(terms); free(next);
+    arena_free(&A);
+}
+
 /* Batched circuit entry points: instances are independent and are spread
  * over threads; each instance is evaluated gate by gate in program order.
  * Return the number of bootstrapped gates evaluated. */
@@ -560,6 +771,48 @@ int64_t orc_mul(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, in
         total += E.gates;
     }
     return total;
+}
+
+typedef void (*orc_circuit_fn)(orc_ev *, int32_t, const uint32_t *, const uint32_t *, uint32_t *);
+
+static int64_t run_batched(orc_circuit_fn fn, const orc_params *P, const uint32_t *bk,
+                           const uint32_t *ksk, int32_t w, int64_t batch, const uint32_t *A,
+                           const uint32_t *B, uint32_t *R, int32_t nthreads)
+{
+    const int64_t num = (int64_t)(P->n + 1) * w;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+#endif
+    for (int64_t b = 0; b < batch; b++) {
+        orc_ev E = {P, bk, ksk, 0};
+        fn(&E, w, A + b * num, B + b * num, R + b * num);
+        total += E.gates;
+    }
+    return total;
+}
+
+int64_t orc_add_maj(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                    int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                    int32_t nthreads)
+{
+    return run_batched(ev_add_maj, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_add_nw(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                   int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                   int32_t nthreads)
+{
+    return run_batched(ev_add_nw, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_mul_tree(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                     int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                     int32_t nthreads)
+{
+    return run_batched(ev_mul_tree, P, bk, ksk, w, batch, A, B, R, nthreads);
 }
 
 int64_t orc_matvec(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,

@@ -21,8 +21,8 @@ LWE_STRIDE = 512
 BIG_STRIDE = 1056
 MU = 1 << 29
 NOALLOC_MAX_GATES = 512
-NAND, AND, OR, XOR, NOR, XNOR = range(6)
-GATE_NAMES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR"]
+NAND, AND, OR, XOR, NOR, XNOR, MAJ, ANDNY, ANDYN, ORNY, ORYN = range(11)
+GATE_NAMES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR", "MAJ", "ANDNY", "ANDYN", "ORNY", "ORYN"]
 
 _STATUS = {0: "TFHE_OK", -1: "TFHE_EINVAL", -2: "TFHE_ENOMEM", -3: "TFHE_ECUDA",
            -4: "TFHE_ETIMEOUT", -5: "TFHE_EBUSY", -6: "TFHE_EDEVICE"}
@@ -98,7 +98,7 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
 }
 
-GATE, ADD, MUL, MATVEC = range(4)
+GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE = range(7)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH = range(6)
 SCHED_ASAP, SCHED_BALANCED = 0, 1
 

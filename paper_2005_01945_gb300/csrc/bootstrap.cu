@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(128) k_bk_to_ntt(const int32_t *__restrict__ b
 
 struct BrArgs {
     DevKeys keys;
-    const int32_t *in_a, *in_b;      // ciphertext bases (row stride kLweStride)
-    const int32_t *idx_a, *idx_b;    // optional gather rows (nullptr: row g)
-    long rows_a, rows_b;             // rows addressable through the bases
+    const int32_t *in_a, *in_b, *in_c;    // ciphertext bases (row stride kLweStride)
+    const int32_t *idx_a, *idx_b, *idx_c; // optional gather rows (nullptr: row g)
+    long rows_a, rows_b, rows_c;          // rows addressable through the bases
     const uint8_t *ops;              // gate opcodes (nullptr: bootstrap in_a as is)
     int32_t *big;                    // out: LWE_N samples [count][kBigStride]
     long count;
@@ -326,15 +326,25 @@ __device__ __forceinline__ void br_crt(BrSmem &S, int p, int h, int lane)
     }
 }
 
-__device__ __forceinline__ void gate_consts(int op, uint32_t &mu, uint32_t &alpha)
+// Linear part of gate `op`: c = mu + aa ca + ab cb + ac cc.  Returns false
+// for an unknown opcode.
+__device__ __forceinline__ bool gate_consts(int op, uint32_t &mu, uint32_t &aa, uint32_t &ab,
+                                            uint32_t &ac)
 {
+    ac = 0u;
     switch (op) {
-    case TFHE_NAND: mu = kMu;           alpha = 0u - 1u; break;
-    case TFHE_AND:  mu = 0u - kMu;      alpha = 1u;      break;
-    case TFHE_OR:   mu = kMu;           alpha = 1u;      break;
-    case TFHE_XOR:  mu = 2u * kMu;      alpha = 2u;      break;
-    case TFHE_NOR:  mu = 0u - kMu;      alpha = 0u - 1u; break;
-    default:        mu = 0u - 2u * kMu; alpha = 0u - 2u; break;  // XNOR
+    case TFHE_NAND:  mu = kMu;           aa = ab = 0u - 1u; return true;
+    case TFHE_AND:   mu = 0u - kMu;      aa = ab = 1u;      return true;
+    case TFHE_OR:    mu = kMu;           aa = ab = 1u;      return true;
+    case TFHE_XOR:   mu = 2u * kMu;      aa = ab = 2u;      return true;
+    case TFHE_NOR:   mu = 0u - kMu;      aa = ab = 0u - 1u; return true;
+    case TFHE_XNOR:  mu = 0u - 2u * kMu; aa = ab = 0u - 2u; return true;
+    case TFHE_MAJ:   mu = 0u;            aa = ab = ac = 1u; return true;
+    case TFHE_ANDNY: mu = 0u - kMu;      aa = 0u - 1u; ab = 1u; return true;
+    case TFHE_ANDYN: mu = 0u - kMu;      aa = 1u; ab = 0u - 1u; return true;
+    case TFHE_ORNY:  mu = kMu;           aa = 0u - 1u; ab = 1u; return true;
+    case TFHE_ORYN:  mu = kMu;           aa = 1u; ab = 0u - 1u; return true;
+    default:         mu = 0u;            aa = ab = 0u;      return false;
     }
 }
 
@@ -356,13 +366,26 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
         // ---- gate combine + mod switch (fused prologue); an empty or bad
         // slot runs with abar = 0 and writes nothing (bad: zero row + flag)
         bool active = g < A.count;
-        long ra = 0, rb = 0;
+        long ra = 0, rb = 0, rc = -1;
+        uint32_t mu_g = 0, aa = 1, ab = 0, ac = 0;
         if (active) {
+            uint32_t err = 0;
+            if (A.ops && !gate_consts(A.ops[g], mu_g, aa, ab, ac))
+                err = kErrOpcode;
             ra = A.idx_a ? (long)A.idx_a[g] : g;
             rb = A.ops ? (A.idx_b ? (long)A.idx_b[g] : g) : 0;
-            if (!(ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b)))) {
+            if (ac) {
+                if (!A.in_c)
+                    err |= kErrOpcode;
+                else
+                    rc = A.idx_c ? (long)A.idx_c[g] : g;
+            }
+            if (!(ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b)) &&
+                  (!ac || !A.in_c || (rc >= 0 && rc < A.rows_c))))
+                err |= kErrGather;
+            if (err) {
                 if (tb == 0)
-                    atomicOr(A.status, kErrGather);
+                    atomicOr(A.status, err);
                 int32_t *bg = A.big + g * kBigStride;
                 for (int k = tb; k <= kN; k += 128)
                     bg[k] = 0;
@@ -372,11 +395,14 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
         if (active) {
             const int32_t *ca = A.in_a + ra * kLweStride;
             const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
-            uint32_t mu_g = 0, alpha = 1;
-            if (A.ops)
-                gate_consts(A.ops[g], mu_g, alpha);
+            const int32_t *cc = ac ? A.in_c + rc * kLweStride : nullptr;
             for (int i = tb; i <= n; i += 128) {
-                uint32_t c = A.ops ? alpha * ((uint32_t)ca[i] + (uint32_t)cb[i]) : (uint32_t)ca[i];
+                uint32_t c = (uint32_t)ca[i];
+                if (A.ops) {
+                    c = aa * c + ab * (uint32_t)cb[i];
+                    if (ac)
+                        c += ac * (uint32_t)cc[i];
+                }
                 if (i == n)
                     c += mu_g;
                 S.abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
@@ -604,7 +630,8 @@ static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const int32_t *in_a,
                                 const int32_t *idx_a, long rows_a, const int32_t *in_b,
                                 const int32_t *idx_b, long rows_b, int32_t *big, long count,
-                                uint32_t mu, uint32_t *status, int grid, cudaStream_t stream)
+                                uint32_t mu, uint32_t *status, int grid, cudaStream_t stream,
+                                const int32_t *in_c, const int32_t *idx_c, long rows_c)
 {
     if (count <= 0)
         return cudaSuccess;
@@ -612,10 +639,13 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     A.keys = keys;
     A.in_a = in_a;
     A.in_b = in_b;
+    A.in_c = in_c;
     A.idx_a = idx_a;
     A.idx_b = idx_b;
+    A.idx_c = idx_c;
     A.rows_a = rows_a;
     A.rows_b = rows_b;
+    A.rows_c = rows_c;
     A.ops = ops;
     A.big = big;
     A.count = count;

@@ -77,6 +77,102 @@ static std::vector<int> build_mul(Netlist &nl, const std::vector<int> &x, const 
     return acc;
 }
 
+// One adder cell over operands that may be the constant 0 (wire -1): with
+// one live operand the sum is that wire, with two a half adder (XOR, AND),
+// with three a full adder, either the ripple form of Eq. "addres" /
+// "addcarry" (p = x^y, s = p^c, carry = (x&y) | (p&c)) or the majority form
+// (carry = MAJ(x, y, c), one bootstrap).  The carry is built only if needed.
+static void adder_cell(Netlist &nl, int x, int y, int cin, bool need_carry, bool maj, int &s,
+                       int &cout)
+{
+    int live[3], k = 0;
+    for (int w : {x, y, cin})
+        if (w >= 0)
+            live[k++] = w;
+    s = cout = -1;
+    if (k == 1) {
+        s = live[0];
+    } else if (k == 2) {
+        s = nl.gate(TFHE_XOR, live[0], live[1]);
+        if (need_carry)
+            cout = nl.gate(TFHE_AND, live[0], live[1]);
+    } else if (k == 3) {
+        const int p = nl.gate(TFHE_XOR, x, y);
+        s = nl.gate(TFHE_XOR, p, cin);
+        if (need_carry) {
+            if (maj) {
+                cout = nl.gate(TFHE_MAJ, x, y, cin);
+            } else {
+                const int g = nl.gate(TFHE_AND, x, y);
+                const int t = nl.gate(TFHE_AND, p, cin);
+                cout = nl.gate(TFHE_OR, g, t);
+            }
+        }
+    }
+}
+
+// w-bit sum (mod 2^w) of two wire vectors with constant-zero entries.
+static std::vector<int> build_add_const(Netlist &nl, const std::vector<int> &x,
+                                        const std::vector<int> &y, bool maj)
+{
+    const int w = (int)x.size();
+    std::vector<int> r(w);
+    int c = -1;
+    for (int i = 0; i < w; ++i)
+        adder_cell(nl, x[i], y[i], c, i < w - 1, maj, r[i], c);
+    return r;
+}
+
+// The paper's number-wise addition GPU_n (section V-B-1): R = A, then w
+// times: C = R AND B, R = R XOR B, B = C << 1 -- both gates on all live
+// bits at once (a compound gate).  Bits of B known to be 0 (shifted in)
+// generate no gates; the carry out of bit w-1 is dropped.
+static std::vector<int> build_add_numberwise(Netlist &nl, const std::vector<int> &x,
+                                             const std::vector<int> &y)
+{
+    const int w = (int)x.size();
+    std::vector<int> R(x), B(y);
+    for (int k = 0; k < w; ++k) {
+        std::vector<int> nR(R), nB(w, -1);
+        for (int i = 0; i < w; ++i) {
+            if (B[i] < 0)
+                continue;
+            nR[i] = nl.gate(TFHE_XOR, R[i], B[i]);
+            if (i + 1 < w)
+                nB[i + 1] = nl.gate(TFHE_AND, R[i], B[i]);
+        }
+        R.swap(nR);
+        B.swap(nB);
+    }
+    return R;
+}
+
+// Truncated multiplication with tree-based accumulation (section V-B-2):
+// partial products A AND b_i shifted by i (low i bits constant 0) are
+// summed pairwise, (0,1), (2,3), ..., an odd last term moving up, with
+// ripple-carry adders that skip constant-zero bits.
+static std::vector<int> build_mul_tree(Netlist &nl, const std::vector<int> &x,
+                                       const std::vector<int> &y)
+{
+    const int w = (int)x.size();
+    std::vector<std::vector<int>> terms;
+    for (int i = 0; i < w; ++i) {
+        std::vector<int> pp(w, -1);
+        for (int j = 0; i + j < w; ++j)
+            pp[i + j] = nl.gate(TFHE_AND, x[j], y[i]);
+        terms.push_back(pp);
+    }
+    while (terms.size() > 1) {
+        std::vector<std::vector<int>> next;
+        for (size_t i = 0; i + 1 < terms.size(); i += 2)
+            next.push_back(build_add_const(nl, terms[i], terms[i + 1], false));
+        if (terms.size() & 1)
+            next.push_back(terms.back());
+        terms.swap(next);
+    }
+    return terms[0];
+}
+
 static std::vector<int> range_wires(int start, int count)
 {
     std::vector<int> v(count);
@@ -103,6 +199,21 @@ bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
         nl.n_in = 2 * w;
         nl.out = kind == TFHE_CIRCUIT_ADD ? build_add(nl, range_wires(0, w), range_wires(w, w))
                                           : build_mul(nl, range_wires(0, w), range_wires(w, w));
+        break;
+    case TFHE_CIRCUIT_ADD_MAJ:
+    case TFHE_CIRCUIT_ADD_NW:
+    case TFHE_CIRCUIT_MUL_TREE:
+        if (w < 1 || w > 64)
+            return false;
+        nl.n_in = 2 * w;
+        nl.out = kind == TFHE_CIRCUIT_ADD_MAJ
+                     ? build_add_const(nl, range_wires(0, w), range_wires(w, w), true)
+                 : kind == TFHE_CIRCUIT_ADD_NW
+                     ? build_add_numberwise(nl, range_wires(0, w), range_wires(w, w))
+                     : build_mul_tree(nl, range_wires(0, w), range_wires(w, w));
+        for (int o : nl.out)
+            if (o < 0)
+                return false;
         break;
     case TFHE_CIRCUIT_MATVEC: {
         if (w < 1 || w > 64 || rows < 1 || cols < 1 || (long)rows * cols > 4096)
@@ -204,7 +315,8 @@ struct Plan {
     int32_t *pool = nullptr;
     int32_t *big = nullptr;
     uint8_t *d_ops = nullptr;
-    int32_t *d_ia = nullptr, *d_ib = nullptr, *d_io = nullptr, *d_out_rows = nullptr;
+    int32_t *d_ia = nullptr, *d_ib = nullptr, *d_ic = nullptr, *d_io = nullptr,
+            *d_out_rows = nullptr;
     std::vector<uint8_t> h_ops;      // host copies for the per-gate schedule
     cudaGraphExec_t graph = nullptr;
     bool graph_failed = false;
@@ -223,6 +335,7 @@ struct Plan {
         cudaFree(d_ops);
         cudaFree(d_ia);
         cudaFree(d_ib);
+        cudaFree(d_ic);
         cudaFree(d_io);
         cudaFree(d_out_rows);
     }
@@ -290,7 +403,8 @@ struct Schedule {
     int depth = 0;
     std::vector<long> level_off;                 // depth + 1 entries
     std::vector<uint8_t> ops;                    // per scheduled gate, level-major
-    std::vector<int32_t> ia, ib, io, outs;
+    std::vector<int32_t> ia, ib, ic, io, outs;
+    bool three = false;                          // some gate has a third input
 };
 
 // Deadline-driven list scheduling (policy TFHE_SCHED_BALANCED): gate g of a
@@ -312,7 +426,7 @@ static void balanced_levels(const std::vector<const Netlist *> &nets, const std:
         const int G = (int)nl.op.size();
         std::vector<int32_t> height(G, 1);
         for (int g = G - 1; g >= 0; --g)
-            for (int in : {nl.a[g], nl.b[g]})
+            for (int in : {nl.a[g], nl.b[g], nl.c[g]})
                 if (in >= nl.n_in)
                     height[in - nl.n_in] = std::max(height[in - nl.n_in], height[g] + 1);
         alap[j].resize(G);
@@ -320,7 +434,7 @@ static void balanced_levels(const std::vector<const Netlist *> &nets, const std:
             alap[j][g] = D + 1 - height[g];
         cons_off[j].assign(G + 1, 0);
         for (int g = 0; g < G; ++g)
-            for (int in : {nl.a[g], nl.b[g]})
+            for (int in : {nl.a[g], nl.b[g], nl.c[g]})
                 if (in >= nl.n_in)
                     cons_off[j][in - nl.n_in + 1]++;
         for (int g = 0; g < G; ++g)
@@ -328,7 +442,7 @@ static void balanced_levels(const std::vector<const Netlist *> &nets, const std:
         cons[j].resize(cons_off[j][G]);
         std::vector<int32_t> fillc(cons_off[j].begin(), cons_off[j].end() - 1);
         for (int g = 0; g < G; ++g)
-            for (int in : {nl.a[g], nl.b[g]})
+            for (int in : {nl.a[g], nl.b[g], nl.c[g]})
                 if (in >= nl.n_in)
                     cons[j][fillc[in - nl.n_in]++] = g;
         node_off[j + 1] = node_off[j] + batch[j] * G;
@@ -348,7 +462,7 @@ static void balanced_levels(const std::vector<const Netlist *> &nets, const std:
         for (long inst = 0; inst < batch[j]; ++inst)
             for (int g = 0; g < G; ++g) {
                 const long id = node_off[j] + inst * G + g;
-                pending[id] = (nl.a[g] >= nl.n_in) + (nl.b[g] >= nl.n_in);
+                pending[id] = (nl.a[g] >= nl.n_in) + (nl.b[g] >= nl.n_in) + (nl.c[g] >= nl.n_in);
                 if (pending[id] == 0)
                     bucket[alap[j][g]].push_back(id);
             }
@@ -454,6 +568,10 @@ static int build_schedule(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int
     S.ia.resize(total);
     S.ib.resize(total);
     S.io.resize(total);
+    for (size_t j = 0; j < njobs; ++j)
+        S.three |= batch[j] > 0 && nets[j]->has3();
+    if (S.three)
+        S.ic.resize(total);
     S.outs.resize(nout);
     std::vector<long> fill(S.level_off.begin(), S.level_off.end());
     for (size_t j = 0; j < njobs; ++j) {
@@ -467,6 +585,8 @@ static int build_schedule(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int
                 S.ops[k] = nl.op[g];
                 S.ia[k] = (int32_t)(b + nl.a[g]);
                 S.ib[k] = (int32_t)(b + nl.b[g]);
+                if (S.three)
+                    S.ic[k] = nl.c[g] >= 0 ? (int32_t)(b + nl.c[g]) : 0;
                 S.io[k] = (int32_t)(b + nl.n_in + g);
             }
             for (size_t o = 0; o < nl.out.size(); ++o)
@@ -509,6 +629,8 @@ static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int p
     alloc((void **)&P.d_ia, std::max(total, 1L) * sizeof(int32_t));
     alloc((void **)&P.d_ib, std::max(total, 1L) * sizeof(int32_t));
     alloc((void **)&P.d_io, std::max(total, 1L) * sizeof(int32_t));
+    if (S.three)
+        alloc((void **)&P.d_ic, std::max(total, 1L) * sizeof(int32_t));
     alloc((void **)&P.d_out_rows, std::max(nout, 1L) * sizeof(int32_t));
     if (e == cudaSuccess && total) {
         e = cudaMemcpy(P.d_ops, S.ops.data(), total, cudaMemcpyHostToDevice);
@@ -518,6 +640,8 @@ static int compile_plan(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, int p
             e = cudaMemcpy(P.d_ib, S.ib.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(P.d_io, S.io.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && S.three)
+            e = cudaMemcpy(P.d_ic, S.ic.data(), total * sizeof(int32_t), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && nout)
         e = cudaMemcpy(P.d_out_rows, S.outs.data(), nout * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -555,7 +679,8 @@ static cudaError_t enqueue_levels(tfhe_ctx *ctx, Plan &P, cudaStream_t st, bool 
         if (e == cudaSuccess)
             e = launch_blind_rotate(ctx->keys, P.d_ops + off, P.pool, P.d_ia + off, P.pool_rows,
                                     P.pool, P.d_ib + off, P.pool_rows, P.big, cnt, kMu,
-                                    ctx->status, ctx->br_grid, st);
+                                    ctx->status, ctx->br_grid, st, P.d_ic ? P.pool : nullptr,
+                                    P.d_ic ? P.d_ic + off : nullptr, P.pool_rows);
         if (e == cudaSuccess)
             e = mark(3 * (l - 1) + 1);
         if (e == cudaSuccess)
@@ -577,7 +702,9 @@ static cudaError_t enqueue_per_gate(tfhe_ctx *ctx, Plan &P, cudaStream_t st)
     for (long k = 0; k < P.gates; ++k) {
         cudaError_t e = launch_blind_rotate(ctx->keys, P.d_ops + k, P.pool, P.d_ia + k, P.pool_rows,
                                             P.pool, P.d_ib + k, P.pool_rows, P.big, 1, kMu,
-                                            ctx->status, ctx->br_grid, st);
+                                            ctx->status, ctx->br_grid, st,
+                                            P.d_ic ? P.pool : nullptr,
+                                            P.d_ic ? P.d_ic + k : nullptr, P.pool_rows);
         if (e != cudaSuccess)
             return e;
         e = launch_keyswitch(ctx->keys.ksk, P.big, P.pool, P.d_io + k, P.pool_rows, 1, ctx->prm.n,

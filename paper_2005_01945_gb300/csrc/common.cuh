@@ -39,6 +39,7 @@ constexpr uint32_t kQ1 = 268367873u;     // 0x0FFEF801
 constexpr uint32_t kErrGather = 1u;
 constexpr uint32_t kErrScatter = 2u;
 constexpr uint32_t kErrTimeout = 4u;
+constexpr uint32_t kErrOpcode = 8u;
 
 #if defined(__CUDACC__)
 // x * w mod q in [0, 2q) for any 32-bit x, with wp = floor(w 2^32 / q)

@@ -12,17 +12,25 @@ namespace tgb {
 struct Netlist {
     int n_in = 0;                    // wires [0, n_in) are inputs
     std::vector<uint8_t> op;         // gate g drives wire n_in + g
-    std::vector<int32_t> a, b;       // input wires of every gate
+    std::vector<int32_t> a, b, c;    // input wires of every gate (c = -1: two inputs)
     std::vector<int32_t> out;        // output wires in output order
     std::vector<int32_t> level;      // ASAP level of every gate (>= 1)
     int depth = 0;
 
-    int gate(int o, int x, int y)
+    int gate(int o, int x, int y, int z = -1)
     {
         op.push_back((uint8_t)o);
         a.push_back(x);
         b.push_back(y);
+        c.push_back(z);
         return n_in + (int)op.size() - 1;
+    }
+    bool has3() const
+    {
+        for (int32_t z : c)
+            if (z >= 0)
+                return true;
+        return false;
     }
     int wires() const { return n_in + (int)op.size(); }
 
@@ -32,7 +40,7 @@ struct Netlist {
         level.resize(op.size());
         depth = 0;
         for (size_t g = 0; g < op.size(); ++g) {
-            const int l = 1 + std::max(wl[a[g]], wl[b[g]]);
+            const int l = 1 + std::max(std::max(wl[a[g]], wl[b[g]]), c[g] >= 0 ? wl[c[g]] : 0);
             level[g] = l;
             wl[n_in + g] = l;
             depth = std::max(depth, l);

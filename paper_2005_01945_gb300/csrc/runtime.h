@@ -58,7 +58,9 @@ int run_bootstrap(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int
 cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const int32_t *in_a,
                                 const int32_t *idx_a, long rows_a, const int32_t *in_b,
                                 const int32_t *idx_b, long rows_b, int32_t *big, long count,
-                                uint32_t mu, uint32_t *status, int grid, cudaStream_t stream);
+                                uint32_t mu, uint32_t *status, int grid, cudaStream_t stream,
+                                const int32_t *in_c = nullptr, const int32_t *idx_c = nullptr,
+                                long rows_c = 0);
 cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
                              const int32_t *idx_out, long rows_out, long count, int n,
                              int num_sms, uint32_t *status, cudaStream_t stream,

@@ -95,7 +95,7 @@ struct SrvReq {
 
 struct Iter {                      // one in-flight iteration (pinned staging + device copy)
     uint8_t *h_ops = nullptr, *d_ops = nullptr;
-    int32_t *h_idx = nullptr, *d_idx = nullptr;  // [3][cap]: a, b, out
+    int32_t *h_idx = nullptr, *d_idx = nullptr;  // [4][cap]: a, b, c, out
     int32_t *h_out = nullptr, *d_out = nullptr;  // output rows of finishing requests
     long cap = 0, out_cap = 0;        // gates / output rows the buffers hold
     cudaEvent_t ev = nullptr;
@@ -191,8 +191,8 @@ static bool iter_reserve(Iter &I, long gates, long outs)
         I.d_idx = I.h_idx = nullptr;
         ok = cudaMalloc(&I.d_ops, c) == cudaSuccess &&
              cudaMallocHost(&I.h_ops, c) == cudaSuccess &&
-             cudaMalloc(&I.d_idx, 3 * c * sizeof(int32_t)) == cudaSuccess &&
-             cudaMallocHost(&I.h_idx, 3 * c * sizeof(int32_t)) == cudaSuccess;
+             cudaMalloc(&I.d_idx, 4 * c * sizeof(int32_t)) == cudaSuccess &&
+             cudaMallocHost(&I.h_idx, 4 * c * sizeof(int32_t)) == cudaSuccess;
         I.cap = ok ? c : 0;
     }
     if (ok && I.out_cap < outs) {
@@ -307,7 +307,8 @@ static void srv_loop(Server *Sp)
                 I.h_ops[k] = nl.op[g];
                 I.h_idx[k] = (int32_t)(r->base + nl.a[g]);
                 I.h_idx[icap + k] = (int32_t)(r->base + nl.b[g]);
-                I.h_idx[2 * icap + k] = (int32_t)(r->base + nl.n_in + g);
+                I.h_idx[2 * icap + k] = nl.c[g] >= 0 ? (int32_t)(r->base + nl.c[g]) : 0;
+                I.h_idx[3 * icap + k] = (int32_t)(r->base + nl.n_in + g);
             }
             if (l == nl.depth)
                 finishing.push_back(r);
@@ -318,7 +319,7 @@ static void srv_loop(Server *Sp)
                 I.h_out[o++] = (int32_t)(r->base + w);
         cudaError_t e = cudaMemcpyAsync(I.d_ops, I.h_ops, count, cudaMemcpyHostToDevice, S.st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(I.d_idx, I.h_idx, 3 * icap * sizeof(int32_t),
+            e = cudaMemcpyAsync(I.d_idx, I.h_idx, 4 * icap * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, S.st);
         if (e == cudaSuccess && nout)
             e = cudaMemcpyAsync(I.d_out, I.h_out, nout * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -326,9 +327,10 @@ static void srv_loop(Server *Sp)
         if (e == cudaSuccess)
             e = launch_blind_rotate(ctx->keys, I.d_ops, S.pool, I.d_idx, S.pool_rows, S.pool,
                                     I.d_idx + icap, S.pool_rows, S.big, count, kMu, ctx->status,
-                                    ctx->br_grid, S.st);
+                                    ctx->br_grid, S.st, S.pool, I.d_idx + 2 * icap,
+                                    S.pool_rows);
         if (e == cudaSuccess)
-            e = launch_keyswitch(ctx->keys.ksk, S.big, S.pool, I.d_idx + 2 * icap, S.pool_rows,
+            e = launch_keyswitch(ctx->keys.ksk, S.big, S.pool, I.d_idx + 3 * icap, S.pool_rows,
                                  count, ctx->prm.n, ctx->num_sms, ctx->status, S.st,
                                  ctx->keys.tune_ks);
         o = 0;

@@ -214,3 +214,50 @@ def test_config3_matvec16(full):
     got = E.host(y)
     assert np.array_equal(E.dec_ints(got), (M * v[None, :]).sum(axis=1) % (1 << 16))
     assert E.ctx.status() == 0
+
+
+@pytest.mark.parametrize("kind_name,w", [("ADD_MAJ", 32), ("ADD_NW", 8), ("MUL_TREE", 8),
+                                         ("ADD_MAJ", 1), ("MUL_TREE", 3)])
+def test_next_circuits_bit_exact(small, kind_name, w):
+    """Majority-carry adder (3-input MAJ gates), the paper's number-wise adder
+    and tree-accumulated multiplication, bit-exact against the oracle."""
+    E = small
+    api = E.api
+    kind = getattr(api, kind_name)
+    a, b = synth.int_pairs(2, w, 11, f"{kind_name}{w}")
+    da, oa = E.enc_ints(a, w, 12, f"na{kind_name}{w}")
+    db, ob = E.enc_ints(b, w, 12, f"nb{kind_name}{w}")
+    R = E.out((2, w))
+    E.ctx.run_jobs([dict(kind=kind, width=w, batch=2, in0=da, in1=db, out=R)])
+    fn = {"ADD_MAJ": E.orc.add_maj, "ADD_NW": E.orc.add_nw, "MUL_TREE": E.orc.mul_tree}[kind_name]
+    want, g = fn(E.P, E.obk, E.oksk, w, oa, ob)
+    got = E.host(R)
+    assert np.array_equal(got, want)
+    assert g == 2 * api.circuit_info(kind, w)[0]
+    assert E.ctx.status() == 0
+
+
+def test_majority_adder_in_serving_and_mixed(small):
+    """3-input gates through the serving loop and in a mixed schedule."""
+    E = small
+    api = E.api
+    a, b = synth.int_pairs(1, 16, 13, "sm16")
+    da, oa = E.enc_ints(a, 16, 14, "sma")
+    db, ob = E.enc_ints(b, 16, 14, "smb")
+    want, _ = E.orc.add_maj(E.P, E.obk, E.oksk, 16, oa, ob)
+    R1, R2, R3 = E.out((1, 16)), E.out((1, 16)), E.out((1, 16))
+    E.ctx.run_jobs([dict(kind=api.ADD_MAJ, width=16, batch=1, in0=da, in1=db, out=R1),
+                    dict(kind=api.ADD, width=16, batch=1, in0=da, in1=db, out=R2)])
+    kd, dv = E.kd, api.to_device
+    bk, ksk = api.keygen(E.p, dv(kd.s), dv(kd.S), dv(kd.bk_mask), dv(kd.bk_noise),
+                         dv(kd.ksk_mask), dv(kd.ksk_noise))
+    ctx = api.Context(E.p)
+    ctx.set_keys(bk, ksk)
+    ctx.serve_start(64 << 20)
+    rid = ctx.serve_submit(api.ADD_MAJ, 16, da[0], db[0], R3[0])
+    ctx.serve_wait(rid, 60000)
+    ctx.serve_stop()
+    ctx.close()
+    assert np.array_equal(E.host(R1), want)
+    assert np.array_equal(E.host(R3), want)
+    assert np.array_equal(E.dec_ints(E.host(R2)), (a + b) % (1 << 16))

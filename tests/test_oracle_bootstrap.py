@@ -106,7 +106,8 @@ def test_keyswitch_noiseless(orc, full):
             assert np.abs(err).max() <= int(kd.S.sum()) * (1 << 15)
 
 
-GATES = {0: "NAND", 1: "AND", 2: "OR", 3: "XOR", 4: "NOR", 5: "XNOR"}
+GATES = {0: "NAND", 1: "AND", 2: "OR", 3: "XOR", 4: "NOR", 5: "XNOR", 7: "ANDNY", 8: "ANDYN",
+         9: "ORNY", 10: "ORYN"}
 
 
 def _truth_tables():
@@ -115,7 +116,7 @@ def _truth_tables():
     tab = {}
     for line in open(path):
         line = line.split("#")[0].split()
-        if len(line) == 5:
+        if len(line) in (5, 9):
             tab[line[0]] = [int(v) for v in line[1:]]
     return tab
 
@@ -162,10 +163,10 @@ def test_gates_full_parameters_truth_tables(orc, full_keys):
     """Every gate on every input pair at the full parameter set."""
     p, P, kd, bk, ksk = full_keys
     tt = _truth_tables()
-    ops = np.repeat(np.arange(6, dtype=np.uint8), 4)
-    a_bits = np.tile(np.array([0, 0, 1, 1], np.uint8), 6)
-    b_bits = np.tile(np.array([0, 1, 0, 1], np.uint8), 6)
-    cd = synth.ct_draws(p, (2, 24), 27, "tt")
+    ops = np.repeat(np.array(sorted(GATES), dtype=np.uint8), 4)
+    a_bits = np.tile(np.array([0, 0, 1, 1], np.uint8), len(GATES))
+    b_bits = np.tile(np.array([0, 1, 0, 1], np.uint8), len(GATES))
+    cd = synth.ct_draws(p, (2, len(ops)), 27, "tt")
     ca = orc.encrypt_bits(P, kd.s, cd.mask[0], cd.noise[0], a_bits)
     cb = orc.encrypt_bits(P, kd.s, cd.mask[1], cd.noise[1], b_bits)
     out = orc.gates(P, bk, ksk, ops, ca, cb)
@@ -175,3 +176,21 @@ def test_gates_full_parameters_truth_tables(orc, full_keys):
     # fresh output noise is far below the 1/8 decision margin
     ph = center(orc.phase(P, kd.s, out))
     assert np.abs(np.abs(ph) - MU).max() < MU // 4
+
+
+def test_majority_gate_truth_table_and_margin(orc, full_keys):
+    """MAJ: noiseless combined phases are +-1/8 or +-3/8 with the sign of the
+    majority; bootstrapped at full parameters it decrypts to the table."""
+    p, P, kd, bk, ksk = full_keys
+    tt = _truth_tables()["MAJ3"]
+    bits = np.array([[(k >> 2) & 1, (k >> 1) & 1, k & 1] for k in range(8)], np.uint8).T
+    cd = synth.ct_draws(p, (3, 8), 28, "maj", noiseless=True)
+    c = [orc.encrypt_bits(P, kd.s, cd.mask[i], cd.noise[i], bits[i]) for i in range(3)]
+    for k in range(8):
+        comb = orc.gate_combine3(P, orc.MAJ, c[0][k], c[1][k], c[2][k])
+        ph = int(center(orc.phase(P, kd.s, comb[None])[0]))
+        assert (ph > 0) == bool(tt[k]) and abs(ph) >= MU
+    cdn = synth.ct_draws(p, (3, 8), 29, "majn")
+    cn = [orc.encrypt_bits(P, kd.s, cdn.mask[i], cdn.noise[i], bits[i]) for i in range(3)]
+    out = np.stack([orc.gate3(P, bk, ksk, orc.MAJ, cn[0][k], cn[1][k], cn[2][k]) for k in range(8)])
+    assert orc.decrypt_bits(P, kd.s, out).tolist() == tt

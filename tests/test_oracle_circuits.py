@@ -142,3 +142,37 @@ def test_balanced_schedule_invariants():
         assert wb.min() > 0
     wb, _ = api.schedule_info([(api.ADD, 32, 0, 0, 256)], api.SCHED_BALANCED, 608)
     assert (wb[:-1] == 608).all() and wb[-1] == 39424 - 61 * 608
+
+
+@pytest.mark.parametrize("name", ["add_maj", "add_nw", "mul_tree"])
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_new_circuits_exhaustive(orc, toy, name, w):
+    """Majority-carry adder, the paper's number-wise adder GPU_n and
+    tree-accumulated multiplication: every input pair at toy parameters."""
+    p, P, kd, bk, ksk = toy
+    a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
+    a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
+    R, g = getattr(orc, name)(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, f"{name}a{w}"),
+                              _enc_ints(orc, p, P, kd, b, w, f"{name}b{w}"))
+    want = (a * b if name == "mul_tree" else a + b) % (1 << w)
+    assert np.array_equal(_dec_ints(orc, P, kd, R), want)
+
+
+@pytest.mark.parametrize("w", [8, 16, 32])
+def test_new_circuits_wide_and_counts(orc, toy, w):
+    """Random wide operands; gate counts: majority adder 3w - 2, number-wise
+    adder w^2, and the oracle's counts equal the CUDA library's netlists
+    (two independent implementations of the circuit definitions)."""
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    p, P, kd, bk, ksk = toy
+    a, b = synth.int_pairs(3, w, 9, f"nc{w}")
+    A, B = _enc_ints(orc, p, P, kd, a, w, "nca"), _enc_ints(orc, p, P, kd, b, w, "ncb")
+    for name, kind, want in (("add_maj", api.ADD_MAJ, (a + b) % (1 << w)),
+                             ("add_nw", api.ADD_NW, (a + b) % (1 << w)),
+                             ("mul_tree", api.MUL_TREE, (a * b) % (1 << w))):
+        R, g = getattr(orc, name)(P, bk, ksk, w, A, B)
+        assert np.array_equal(_dec_ints(orc, P, kd, R), want), name
+        assert g == 3 * api.circuit_info(kind, w)[0], name
+    assert api.circuit_info(api.ADD_MAJ, w) == (3 * w - 2, w)
+    assert api.circuit_info(api.ADD_NW, w) == (w * w, w)
