@@ -107,8 +107,9 @@ def br_traffic_per_launch():
     try:
         fields = {}
         for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
-            if ":" in line and line.strip().startswith(("bytes_per_launch", "kernel_source_sha1")):
-                k, v = line.strip().split(":", 1)
+            line = line.strip().lstrip("-* ")
+            if ":" in line and line.startswith(("bytes_per_launch", "kernel_source_sha1")):
+                k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
         if fields.get("kernel_source_sha1") != kernel_source_sha1():
             return None
