@@ -274,8 +274,9 @@ def run_br_only(count, group=0):
 
 def run_variants(args):
     """Circuit variants of the paper (sections V-A, V-B): adders (ripple carry,
-    majority carry, number-wise GPU_n) and multipliers (sequential, tree
-    accumulation), as batches and as single-request latency; and the
+    majority carry, number-wise GPU_n), truncated multipliers (sequential,
+    tree accumulation) and full products (naive, Karatsuba), as batches and
+    as single-request latency; and the
     compound-gate ablation (section V-A-3, Fig. "compoundGateAna"): the XOR
     and AND of two w-bit numbers as two launches or as one."""
     import torch
@@ -337,6 +338,29 @@ def run_variants(args):
                                        "gates_per_s": 64 * g / (ms / 1e3),
                                        "single_ms": timed(lambda: ctx.run_jobs(one), 5),
                                        "verified": ok}
+    def dec_wide(t):
+        bits = api.decrypt_bits(p, s_dev, t).cpu().numpy()
+        return [sum(int(v) << i for i, v in enumerate(row)) for row in bits]
+
+    # full products (2w bits): naive with tree accumulation vs Karatsuba
+    # (section III-B, Table "multiplicationComparison")
+    res["full_products"] = {}
+    for w, batch in ((16, 64), (32, 32), (64, 8)):
+        fa, fb = synth.int_pairs(batch, w, seed, f"var_full{w}")
+        FA, FB = enc(fa, w, f"vfa{w}"), enc(fb, w, f"vfb{w}")
+        FR = torch.empty((batch, 2 * w, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+        want = [int(x) * int(y) for x, y in zip(fa, fb)]
+        entry = {}
+        for name, kind in (("naive", api.MUL_FULL), ("karatsuba", api.MUL_KARATSUBA)):
+            job = [dict(kind=kind, width=w, batch=batch, in0=FA, in1=FB, out=FR)]
+            ms = timed(lambda: ctx.run_jobs(job), 2)
+            ok = dec_wide(FR) == want
+            g, depth = api.circuit_info(kind, w)
+            one = [dict(kind=kind, width=w, batch=1, in0=FA[:1], in1=FB[:1], out=FR[:1])]
+            entry[name] = {f"batch{batch}_ms": ms, "gates": batch * g, "depth": depth,
+                           "gates_per_s": batch * g / (ms / 1e3),
+                           "single_ms": timed(lambda: ctx.run_jobs(one), 3), "verified": ok}
+        res["full_products"][f"{w}x{w}"] = entry
     for w in (1, 2, 4, 8, 16, 32):
         x, y = synth.int_pairs(1, w, seed, f"cg{w}")
         X, Y = enc(x, w, f"cgx{w}")[0], enc(y, w, f"cgy{w}")[0]

@@ -190,8 +190,16 @@ typedef enum {
     TFHE_CIRCUIT_ADD_NW = 5,   /* the paper's number-wise adder GPU_n (section    */
                                /*   V-B-1): w rounds of (R AND B, R XOR B, B<<1),  */
                                /*   w^2 gates, depth w                            */
-    TFHE_CIRCUIT_MUL_TREE = 6  /* multiplication with tree-based accumulation    */
+    TFHE_CIRCUIT_MUL_TREE = 6, /* multiplication with tree-based accumulation    */
                                /*   of the partial products (section V-B-2)       */
+    TFHE_CIRCUIT_MUL_FULL = 7, /* full product, w x w -> 2w bits, 2 <= w <= 64:  */
+                               /*   AND partial products at their weights summed  */
+                               /*   by the tree of section V-B-2                  */
+    TFHE_CIRCUIT_MUL_KARATSUBA = 8 /* full product by Karatsuba (Algorithm        */
+                               /*   "karatsuba", vector form of section V-B),     */
+                               /*   split at ceil(w/2), Z2 - (Z0 + Z1) by a       */
+                               /*   two's-complement subtractor, the full product */
+                               /*   above below 8 bits; 2w bits, 2 <= w <= 64     */
 } tfhe_circuit;
 
 typedef struct {
@@ -201,7 +209,8 @@ typedef struct {
     int64_t batch;          /* independent instances                              */
     const int32_t *in0;     /* A (GATE/ADD/MUL) or M (MATVEC), device, [batch]... */
     const int32_t *in1;     /* B or v, device                                     */
-    int32_t *out;           /* R or y, device                                     */
+    int32_t *out;           /* R or y, device; [batch][w][512] except MUL_FULL    */
+                            /* and MUL_KARATSUBA: [batch][2w][512]                */
 } tfhe_job;
 
 int tfhe_run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, void *stream);

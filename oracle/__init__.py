@@ -80,6 +80,8 @@ def lib():
             "orc_add_maj": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_add_nw": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_tree": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_mul_full": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_mul_karatsuba": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_blind_rotate_many": (None, [P, vp, i64, vp, u32, vp, i32]),
             "orc_sample_extract": (None, [i32, vp, vp]),
             "orc_keyswitch_many": (None, [P, vp, i64, vp, vp]),
@@ -271,6 +273,26 @@ def add_nw(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
 def mul_tree(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
     """Multiplication with tree-based accumulation -> (R, gates)."""
     return _circuit("orc_mul_tree", P, bk, ksk, w, A, B, nthreads)
+
+
+def _full(name, P, bk, ksk, w, A, B, nthreads):
+    bk, ksk, A, B = _u32(bk), _u32(ksk), _u32(A), _u32(B)
+    batch = A.size // (w * (P.n + 1))
+    R = np.empty((batch, 2 * w, P.n + 1), dtype=np.uint32)
+    g = getattr(lib(), name)(ctypes.byref(P), _p(bk), _p(ksk), w, batch, _p(A), _p(B), _p(R),
+                             nthreads)
+    return R, int(g)
+
+
+def mul_full(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Full product (2w bits), partial products summed by the tree ->
+    (R [batch][2w][n+1], gates)."""
+    return _full("orc_mul_full", P, bk, ksk, w, A, B, nthreads)
+
+
+def mul_karatsuba(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Karatsuba full product (2w bits) -> (R [batch][2w][n+1], gates)."""
+    return _full("orc_mul_karatsuba", P, bk, ksk, w, A, B, nthreads)
 
 
 def gate3(P: Params, bk, ksk, op: int, ca, cb, cc) -> np.ndarray:

@@ -734,6 +734,187 @@ static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t
     arena_free(&A);
 }
 
+/* Full product Z = X Y of n-bit X, Y as 2n bits (section III-B-1, "Naive
+ * Approach", without truncation): partial product i is X AND y_i moved up by
+ * i bits, so it covers weights i .. i+n-1 of the 2n; the n partial products
+ * are then summed by the tree of section V-B-2 with 2n-bit adders. */
+static void ev_full_product(orc_ev *E, orc_arena *A, int32_t n, const uint32_t **x,
+                            const uint32_t **y, const uint32_t **z)
+{
+    const int32_t w = 2 * n;
+    const uint32_t **terms = calloc((size_t)n * w, sizeof(*terms));
+    const uint32_t **next = calloc((size_t)n * w, sizeof(*next));
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t j = 0; j < n; j++) {
+            uint32_t *pp = arena_new(A);
+            ev_gate(E, ORC_AND, x[j], y[i], pp);
+            terms[i * w + i + j] = pp;
+        }
+    int32_t cnt = n;
+    while (cnt > 1) {
+        int32_t k = 0;
+        for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
+            ev_add_cells(E, A, w, terms + i * w, terms + (i + 1) * w, 0, next + k * w);
+        if (cnt & 1) {
+            memcpy(next + k * w, terms + (cnt - 1) * w, sizeof(*terms) * w);
+            k++;
+        }
+        memcpy(terms, next, sizeof(*terms) * w * k);
+        cnt = k;
+    }
+    memcpy(z, terms, sizeof(*terms) * w);
+    free(terms); free(next);
+}
+
+/* D = S - T mod 2^L for L-bit S (every bit an encrypted wire) and m-bit T,
+ * m <= L: the two's-complement form S + T' + 1 of the paper's last step of
+ * the vector Karatsuba (section V-B, "Karatsuba Multiplication"), with the
+ * +1 entering as the carry into bit 0 and the complement of T folded into
+ * the gates, since negating a ciphertext is the free NOT of TFHE:
+ *   bit 0, carry-in 1:      d = s XOR t,            carry = s OR NOT t
+ *   bit i < m, carry c:     e = s XNOR t,  d = e XOR c,
+ *                           carry = (s AND NOT t) OR (e AND c)
+ *   bit i >= m (t' = 1):    d = s XNOR c,           carry = s OR c
+ * The carry out of bit L-1 is not formed. */
+static void ev_sub(orc_ev *E, orc_arena *A, int32_t L, const uint32_t **S, int32_t m,
+                   const uint32_t **T, const uint32_t **D)
+{
+    const uint32_t *c = NULL;
+    for (int32_t i = 0; i < L; i++) {
+        const int carry = i < L - 1;
+        uint32_t *d = arena_new(A);
+        uint32_t *co = carry ? arena_new(A) : NULL;
+        if (i == 0) {
+            ev_gate(E, ORC_XOR, S[0], T[0], d);
+            if (carry)
+                ev_gate(E, ORC_ORYN, S[0], T[0], co);
+        } else if (i < m) {
+            uint32_t *e = arena_new(A);
+            ev_gate(E, ORC_XNOR, S[i], T[i], e);
+            ev_gate(E, ORC_XOR, e, c, d);
+            if (carry) {
+                uint32_t *g = arena_new(A), *t = arena_new(A);
+                ev_gate(E, ORC_ANDYN, S[i], T[i], g);
+                ev_gate(E, ORC_AND, e, c, t);
+                ev_gate(E, ORC_OR, g, t, co);
+            }
+        } else {
+            ev_gate(E, ORC_XNOR, S[i], c, d);
+            if (carry)
+                ev_gate(E, ORC_OR, S[i], c, co);
+        }
+        D[i] = d;
+        c = co;
+    }
+}
+
+/* Sum with carry out: R (max(lx, ly) + 1 bits) = X (lx bits) + Y (ly bits). */
+static void ev_add_ext(orc_ev *E, orc_arena *A, int32_t lx, const uint32_t **X, int32_t ly,
+                       const uint32_t **Y, const uint32_t **R)
+{
+    const int32_t L = (lx > ly ? lx : ly) + 1;
+    const uint32_t **x = calloc(L, sizeof(*x)), **y = calloc(L, sizeof(*y));
+    memcpy(x, X, sizeof(*x) * lx);
+    memcpy(y, Y, sizeof(*y) * ly);
+    ev_add_cells(E, A, L, x, y, 0, R);
+    free(x); free(y);
+}
+
+/* Karatsuba multiplication (Algorithm "karatsuba", with the vector form of
+ * section V-B): Z (2n bits) = X Y.  Below n0 = ORC_KARATSUBA_N0 bits the base
+ * multiplication is the full product above.  Otherwise, with h = ceil(n/2):
+ *   X0 = X mod 2^h, X1 = X / 2^h, Y0, Y1 likewise
+ *   <Temp0, Temp1> = <X0, Y0> + <X1, Y1>            (h + 1 bits each)
+ *   <Z0, Z1, Z2>   = <X0, X1, Temp0> . <Y0, Y1, Temp1>
+ *   Temp1 = Z1 + Z0;  Z2 = Z2 - Temp1               (= X0 Y1 + X1 Y0)
+ *   Z = Z0 + Z2 2^h + Z1 2^(2h)                    (mod 2^(2n))
+ * The first and last terms do not overlap (Z0 has 2h bits), so they are
+ * placed side by side and one 2n-bit addition adds the middle term. */
+#define ORC_KARATSUBA_N0 8
+static void ev_karatsuba(orc_ev *E, orc_arena *A, int32_t n, const uint32_t **X,
+                         const uint32_t **Y, const uint32_t **Z)
+{
+    if (n < ORC_KARATSUBA_N0) {
+        ev_full_product(E, A, n, X, Y, Z);
+        return;
+    }
+    const int32_t h = (n + 1) / 2, m = n - h;
+    const uint32_t **t0 = malloc(sizeof(*t0) * (h + 1)), **t1 = malloc(sizeof(*t1) * (h + 1));
+    const uint32_t **z0 = malloc(sizeof(*z0) * 2 * h), **z1 = malloc(sizeof(*z1) * 2 * m);
+    const uint32_t **z2 = malloc(sizeof(*z2) * (2 * h + 2)), **u = malloc(sizeof(*u) * (2 * h + 1));
+    const uint32_t **d = malloc(sizeof(*d) * (2 * h + 2));
+    const uint32_t **lo = calloc(2 * n, sizeof(*lo)), **mid = calloc(2 * n, sizeof(*mid));
+    ev_add_ext(E, A, h, X, m, X + h, t0);
+    ev_add_ext(E, A, h, Y, m, Y + h, t1);
+    ev_karatsuba(E, A, h, X, Y, z0);
+    ev_karatsuba(E, A, m, X + h, Y + h, z1);
+    ev_karatsuba(E, A, h + 1, t0, t1, z2);
+    ev_add_ext(E, A, 2 * h, z0, 2 * m, z1, u);
+    ev_sub(E, A, 2 * h + 2, z2, 2 * h + 1, u, d);
+    for (int32_t i = 0; i < 2 * h; i++)
+        lo[i] = z0[i];
+    for (int32_t i = 0; i < 2 * m; i++)
+        lo[2 * h + i] = z1[i];
+    for (int32_t i = 0; i < 2 * h + 2 && h + i < 2 * n; i++)
+        mid[h + i] = d[i];
+    ev_add_cells(E, A, 2 * n, lo, mid, 0, Z);
+    free(t0); free(t1); free(z0); free(z1); free(z2); free(u); free(d); free(lo); free(mid);
+}
+
+typedef void (*orc_full_fn)(orc_ev *, orc_arena *, int32_t, const uint32_t **, const uint32_t **,
+                            const uint32_t **);
+
+/* Batched full products: A, B [batch][w][n+1] -> R [batch][2w][n+1]. */
+static int64_t run_full(orc_full_fn fn, const orc_params *P, const uint32_t *bk,
+                        const uint32_t *ksk, int32_t w, int64_t batch, const uint32_t *Av,
+                        const uint32_t *Bv, uint32_t *R, int32_t nthreads)
+{
+    const int64_t W = P->n + 1, num = W * w;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+#endif
+    for (int64_t b = 0; b < batch; b++) {
+        orc_ev E = {P, bk, ksk, 0};
+        orc_arena A = {NULL, 0, 0, W};
+        const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
+                       **z = malloc(sizeof(*z) * 2 * w);
+        for (int32_t i = 0; i < w; i++) {
+            x[i] = Av + b * num + i * W;
+            y[i] = Bv + b * num + i * W;
+        }
+        fn(&E, &A, w, x, y, z);
+        for (int32_t i = 0; i < 2 * w; i++) {
+            if (z[i])
+                memcpy(R + 2 * b * num + i * W, z[i], sizeof(uint32_t) * W);
+            else {  /* a constant-0 bit: the trivial sample (0, ..., 0, -1/8) */
+                memset(R + 2 * b * num + i * W, 0, sizeof(uint32_t) * W);
+                R[2 * b * num + i * W + P->n] = (uint32_t)-(1u << 29);
+            }
+        }
+        free(x); free(y); free(z);
+        arena_free(&A);
+        total += E.gates;
+    }
+    return total;
+}
+
+int64_t orc_mul_full(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                     int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                     int32_t nthreads)
+{
+    return run_full(ev_full_product, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_mul_karatsuba(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                          int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                          int32_t nthreads)
+{
+    return run_full(ev_karatsuba, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
 /* Batched circuit entry points: instances are independent and are spread
  * over threads; each instance is evaluated gate by gate in program order.
  * Return the number of bootstrapped gates evaluated. */

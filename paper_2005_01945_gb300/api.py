@@ -98,7 +98,7 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
 }
 
-GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE = range(7)
+GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA = range(9)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH = range(6)
 SCHED_ASAP, SCHED_BALANCED = 0, 1
 

@@ -173,6 +173,113 @@ static std::vector<int> build_mul_tree(Netlist &nl, const std::vector<int> &x,
     return terms[0];
 }
 
+// Full product of two wire vectors (len(x) = len(y) = n -> 2n bits):
+// partial products at their weights, summed by the same pairwise tree.
+static std::vector<int> build_mul_full(Netlist &nl, const std::vector<int> &x,
+                                       const std::vector<int> &y)
+{
+    const int n = (int)x.size(), w = 2 * n;
+    std::vector<std::vector<int>> terms;
+    for (int i = 0; i < n; ++i) {
+        std::vector<int> pp(w, -1);
+        for (int j = 0; j < n; ++j)
+            pp[i + j] = nl.gate(TFHE_AND, x[j], y[i]);
+        terms.push_back(pp);
+    }
+    while (terms.size() > 1) {
+        std::vector<std::vector<int>> next;
+        for (size_t i = 0; i + 1 < terms.size(); i += 2)
+            next.push_back(build_add_const(nl, terms[i], terms[i + 1], false));
+        if (terms.size() & 1)
+            next.push_back(terms.back());
+        terms.swap(next);
+    }
+    return terms[0];
+}
+
+// Sum with carry out: max(len) + 1 bits.
+static std::vector<int> build_add_ext(Netlist &nl, std::vector<int> x, std::vector<int> y)
+{
+    const size_t L = std::max(x.size(), y.size()) + 1;
+    x.resize(L, -1);
+    y.resize(L, -1);
+    return build_add_const(nl, x, y, false);
+}
+
+// a - b mod 2^len(a) = a + NOT b + 1 for len(b) <= len(a), every bit of a
+// live.  Cells: with the carry-in 1 of bit 0, sum a XOR b and carry
+// a OR NOT b (ORYN); with a live carry, p = a XNOR b, sum p XOR c, carry
+// (a AND NOT b) OR (p AND c); past the end of b (NOT 0 = 1), sum a XNOR c
+// and carry a OR c.  Returns false if a case outside these arises.
+static bool build_sub(Netlist &nl, const std::vector<int> &a, const std::vector<int> &b,
+                      std::vector<int> &r)
+{
+    const int L = (int)a.size();
+    r.assign(L, -1);
+    int c = -2;  // -2: the constant 1
+    for (int i = 0; i < L; ++i) {
+        const bool need = i < L - 1;
+        const int bi = i < (int)b.size() ? b[i] : -1;
+        if (a[i] < 0)
+            return false;
+        if (bi >= 0 && c == -2) {
+            r[i] = nl.gate(TFHE_XOR, a[i], bi);
+            c = need ? nl.gate(TFHE_ORYN, a[i], bi) : -1;
+        } else if (bi >= 0 && c >= 0) {
+            const int p = nl.gate(TFHE_XNOR, a[i], bi);
+            r[i] = nl.gate(TFHE_XOR, p, c);
+            if (need) {
+                const int g = nl.gate(TFHE_ANDYN, a[i], bi);
+                const int t = nl.gate(TFHE_AND, p, c);
+                c = nl.gate(TFHE_OR, g, t);
+            }
+        } else if (bi < 0 && c >= 0) {
+            r[i] = nl.gate(TFHE_XNOR, a[i], c);
+            c = need ? nl.gate(TFHE_OR, a[i], c) : -1;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+// Karatsuba multiplication (Algorithm "karatsuba"; the printed recombination
+// is garbled -- here the textbook form): for n-bit X, Y with n >= n0,
+// h = ceil(n/2), X = X0 + X1 2^h, Y likewise;
+//   Z0 = K(X0, Y0), Z1 = K(X1, Y1), Z2 = K(X0 + X1, Y0 + Y1)  (sums carry out)
+//   M  = Z2 - (Z0 + Z1) = X0 Y1 + X1 Y0
+//   Z  = (Z0 + Z1 2^(2h)) + M 2^h                 (2n bits)
+// The first term is Z0 and Z1 side by side (no gates).  Below n0 the full
+// product is formed directly.
+static bool build_karatsuba(Netlist &nl, const std::vector<int> &x, const std::vector<int> &y,
+                            int n0, std::vector<int> &z)
+{
+    const int n = (int)x.size();
+    if (n < n0) {
+        z = build_mul_full(nl, x, y);
+        return true;
+    }
+    const int h = (n + 1) / 2;
+    std::vector<int> x0(x.begin(), x.begin() + h), x1(x.begin() + h, x.end());
+    std::vector<int> y0(y.begin(), y.begin() + h), y1(y.begin() + h, y.end());
+    std::vector<int> z0, z1, z2, m;
+    if (!build_karatsuba(nl, x0, y0, n0, z0) || !build_karatsuba(nl, x1, y1, n0, z1))
+        return false;
+    std::vector<int> sx = build_add_ext(nl, x0, x1), sy = build_add_ext(nl, y0, y1);
+    if (!build_karatsuba(nl, sx, sy, n0, z2))
+        return false;
+    std::vector<int> u = build_add_ext(nl, z0, z1);
+    if (!build_sub(nl, z2, u, m))
+        return false;
+    std::vector<int> t(z0);
+    t.insert(t.end(), z1.begin(), z1.end());       // Z0 + Z1 2^(2h), 2n bits
+    std::vector<int> ms(2 * n, -1);
+    for (int i = 0; i < (int)m.size() && h + i < 2 * n; ++i)
+        ms[h + i] = m[i];
+    z = build_add_const(nl, t, ms, false);
+    return true;
+}
+
 static std::vector<int> range_wires(int start, int count)
 {
     std::vector<int> v(count);
@@ -215,6 +322,20 @@ bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
             if (o < 0)
                 return false;
         break;
+    case TFHE_CIRCUIT_MUL_FULL:
+    case TFHE_CIRCUIT_MUL_KARATSUBA: {
+        if (w < 2 || w > 64)   // at w = 1 the top product bit is the constant 0
+            return false;
+        nl.n_in = 2 * w;
+        if (kind == TFHE_CIRCUIT_MUL_FULL)
+            nl.out = build_mul_full(nl, range_wires(0, w), range_wires(w, w));
+        else if (!build_karatsuba(nl, range_wires(0, w), range_wires(w, w), 8, nl.out))
+            return false;
+        for (int o : nl.out)
+            if (o < 0)
+                return false;
+        break;
+    }
     case TFHE_CIRCUIT_MATVEC: {
         if (w < 1 || w > 64 || rows < 1 || cols < 1 || (long)rows * cols > 4096)
             return false;

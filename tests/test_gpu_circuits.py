@@ -261,3 +261,41 @@ def test_majority_adder_in_serving_and_mixed(small):
     assert np.array_equal(E.host(R1), want)
     assert np.array_equal(E.host(R3), want)
     assert np.array_equal(E.dec_ints(E.host(R2)), (a + b) % (1 << 16))
+
+
+@pytest.mark.parametrize("kind_name,w", [("MUL_FULL", 2), ("MUL_FULL", 8), ("MUL_KARATSUBA", 9),
+                                         ("MUL_KARATSUBA", 16), ("MUL_KARATSUBA", 32)])
+def test_full_products_bit_exact(small, kind_name, w):
+    """Full products (2w output rows): the naive product and Karatsuba
+    (Algorithm "karatsuba", vector form of section V-B), bit-exact against
+    the oracle, with all-ones operands among the instances."""
+    E = small
+    api = E.api
+    kind = getattr(api, kind_name)
+    a, b = synth.int_pairs(2, w, 13, f"{kind_name}{w}")
+    a[0] = b[0] = (1 << w) - 1
+    da, oa = E.enc_ints(a, w, 14, f"fa{kind_name}{w}")
+    db, ob = E.enc_ints(b, w, 14, f"fb{kind_name}{w}")
+    R = E.out((2, 2 * w))
+    E.ctx.run_jobs([dict(kind=kind, width=w, batch=2, in0=da, in1=db, out=R)])
+    fn = E.orc.mul_full if kind_name == "MUL_FULL" else E.orc.mul_karatsuba
+    want, g = fn(E.P, E.obk, E.oksk, w, oa, ob)
+    got = E.host(R)
+    assert np.array_equal(got, want)
+    assert g == 2 * api.circuit_info(kind, w)[0]
+    bits = E.orc.decrypt_bits(E.P, E.kd.s, got)
+    assert [sum(int(v) << i for i, v in enumerate(r)) for r in bits] == \
+        [int(x) * int(y) for x, y in zip(a, b)]
+    assert E.ctx.status() == 0
+
+
+def test_full_product_width_checked(small):
+    """w = 1 has a constant top product bit and is refused; so is w > 64."""
+    E = small
+    api = E.api
+    R = E.out((1, 2))
+    A = E.out((1, 1))
+    for w in (1, 65):
+        with pytest.raises(RuntimeError):
+            E.ctx.run_jobs([dict(kind=api.MUL_KARATSUBA, width=w, batch=1, in0=A, in1=A, out=R)])
+    assert E.ctx.status() == 0

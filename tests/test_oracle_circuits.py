@@ -176,3 +176,50 @@ def test_new_circuits_wide_and_counts(orc, toy, w):
         assert g == 3 * api.circuit_info(kind, w)[0], name
     assert api.circuit_info(api.ADD_MAJ, w) == (3 * w - 2, w)
     assert api.circuit_info(api.ADD_NW, w) == (w * w, w)
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_full_products_exhaustive(orc, toy, w):
+    """Full products (2w bits): the naive product and Karatsuba (which is
+    the naive product below its 8-bit base case) on every input pair."""
+    p, P, kd, bk, ksk = toy
+    a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
+    a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
+    A = _enc_ints(orc, p, P, kd, a, w, f"fpa{w}")
+    B = _enc_ints(orc, p, P, kd, b, w, f"fpb{w}")
+    for name in ("mul_full", "mul_karatsuba"):
+        R, g = getattr(orc, name)(P, bk, ksk, w, A, B)
+        assert R.shape == (len(a), 2 * w, P.n + 1)
+        assert np.array_equal(_dec_ints(orc, P, kd, R), a * b), name
+
+
+def _edge_pairs(w, n, seed, tag):
+    """Random w-bit pairs plus the operands that drive the longest carry and
+    borrow chains: all ones, a lone top bit, zero, one."""
+    top, ones = 1 << (w - 1), (1 << w) - 1
+    ea = np.array([ones, ones, top, top, 0, ones, 1, top | 1], dtype=np.uint64)
+    eb = np.array([ones, 1, top, ones, ones, 0, ones, ones], dtype=np.uint64)
+    a, b = synth.int_pairs(n, w, seed, tag)
+    return np.concatenate([ea, a]), np.concatenate([eb, b])
+
+
+@pytest.mark.parametrize("w", [8, 9, 16, 17, 32])
+def test_karatsuba_products(orc, toy, w):
+    """Karatsuba (Algorithm "karatsuba" in the vector form of section V-B)
+    against the integer product, at widths that recurse once (8, 9: odd
+    split), twice (16, 17) and three times (32), with the edge operands
+    that exercise the subtraction Z2 - (Z0 + Z1) over its full width; the
+    oracle's gate counts equal the CUDA library's netlists."""
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    p, P, kd, bk, ksk = toy
+    a, b = _edge_pairs(w, 120 if w <= 9 else 24, 17, f"ka{w}")
+    A = _enc_ints(orc, p, P, kd, a, w, f"kaa{w}")
+    B = _enc_ints(orc, p, P, kd, b, w, f"kab{w}")
+    want = [int(x) * int(y) for x, y in zip(a, b)]
+    for name, kind in (("mul_karatsuba", api.MUL_KARATSUBA), ("mul_full", api.MUL_FULL)):
+        R, g = getattr(orc, name)(P, bk, ksk, w, A, B)
+        bits = orc.decrypt_bits(P, kd.s, R)
+        got = [sum(int(v) << i for i, v in enumerate(row)) for row in bits]
+        assert got == want, name
+        assert g == len(a) * api.circuit_info(kind, w)[0], name
