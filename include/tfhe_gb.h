@@ -241,8 +241,10 @@ typedef enum {
     TFHE_OPT_PROFILE = 2,    /* 1: record CUDA events around every blind-rotation   */
                              /*    and key-switch launch of circuit schedules (also */
                              /*    inside captured graphs)                          */
-    TFHE_OPT_BR_GROUP = 3,   /* bootstraps per blind-rotation CTA: 1, 2 or 4, or 0  */
-                             /*    (default) to choose by batch size                */
+    TFHE_OPT_BR_GROUP = 3,   /* blind-rotation CTA shape: 1, 2 or 4 bootstraps per  */
+                             /*    CTA (4 warps each), 8 = one bootstrap on 8 warps */
+                             /*    (lower latency), or 0 (default): autotuned, else */
+                             /*    by batch size                                    */
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
     TFHE_OPT_LEVEL_WIDTH = 5 /* target gates per level for BALANCED (0: one wave,   */
                              /*    4 bootstraps per SM)                             */

@@ -271,6 +271,32 @@ __device__ __forceinline__ void br_digits_fwd(uint32_t (&x)[32], BrSmem &S, int 
     }
 }
 
+// Phase 1 with eight warps per bootstrap: warp (c, j, h) forms digit
+// polynomial j of TLWE polynomial c of X^a acc - acc and transforms it
+// modulo prime h into S.fwd[2c + j][h] (its own slot, also the transpose
+// scratch).
+__device__ __forceinline__ void br_digit_fwd(uint32_t (&x)[32], BrSmem &S, int c, int j, int a,
+                                             int lane, const uint2 *__restrict__ twb,
+                                             const Prime &pr)
+{
+    const uint32_t *ac = S.acc[c];
+    uint32_t *sj = S.fwd[2 * c + j][pr.P];
+    const int shift = j ? 12 : 22;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int k = lane + 32 * r;
+        const int idx = (k - a) & (2 * kN - 1);
+        uint32_t v = ac[idx & (kN - 1)];
+        v = idx >= kN ? 0u - v : v;
+        const uint32_t u = v - ac[k] + kDecompOffset;
+        x[r] = ((u >> shift) & 1023u) + (pr.q - 512u);
+    }
+    fwd_ntt(x, sj, lane, twb, pr);
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        sj[r * 32 + lane] = x[r];
+}
+
 // Phase 2: pointwise products for output polynomial p modulo prime h,
 // summed over the 4 digit rows; result in [0, 2q).
 __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
@@ -311,15 +337,17 @@ __device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4,
 // exact coefficient S satisfies |S| <= 4 N 2^9 2^31 = 2^52, so for S >= 0
 // u = floor(S / q0) < 2^25, and for S < 0 (v = S + q0 q1) u > q1 - 2^25:
 // the centring decision (v >= q0 q1 / 2) is exactly u > (q1 - 1) / 2.
-__device__ __forceinline__ void br_crt(BrSmem &S, int p, int h, int lane)
+// The calling warp lifts registers r0 .. r0 + NR - 1 of polynomial p.
+template <int NR>
+__device__ __forceinline__ void br_crt(BrSmem &S, int p, int r0, int lane)
 {
     const uint32_t *x0 = S.fwd[p * 2 + 0][1], *x1 = S.fwd[p * 2 + 1][1];
     const uint32_t c = c_ntt.crt_c, cp = c_ntt.crt_cp, plo = c_ntt.p_lo;
     constexpr uint32_t uh = (kQ1 - 1) / 2;
     uint32_t *acc = S.acc[p];
 #pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-        const int e = (16 * h + rr) * 32 + lane;
+    for (int rr = 0; rr < NR; ++rr) {
+        const int e = (r0 + rr) * 32 + lane;
         const uint32_t r0 = x0[e], r1 = x1[e];
         const uint32_t u = csub(mul_shoup(r1 - r0 + 2 * kQ1, c, cp, kQ1), kQ1);
         acc[e] += r0 + kQ0 * u - (u > uh ? plo : 0u);
@@ -348,17 +376,25 @@ __device__ __forceinline__ bool gate_consts(int op, uint32_t &mu, uint32_t &aa, 
     }
 }
 
-// B bootstraps per CTA (4B warps); 128 registers per thread, 16 warps/SM.
-template <int B>
-__global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
+// B bootstraps per CTA, W warps each (W = 4: B in {1, 2, 4} in lockstep;
+// W = 8: B = 1, the phases spread over twice the warps for lower latency on
+// narrow levels); 128 registers per thread, 16 warps/SM.
+//   W = 4: warp (p, h) runs phase 1 as (c = p, both digits), phases 2-3 as
+//          output polynomial p modulo prime h, phase 4 on half of p.
+//   W = 8: warp (c, j, h) runs phase 1 for digit j of polynomial c; warps
+//          0..3 run phases 2-3 as (p, h); every warp runs phase 4 on a
+//          quarter of polynomial w >> 2.
+template <int B, int W>
+__global__ void __launch_bounds__(32 * W * B, 16 / (W * B)) k_blind_rotate(const BrArgs A)
 {
+    constexpr int T = 32 * W;      // threads per bootstrap
     extern __shared__ uint4 smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bi = warp >> 2, w4 = warp & 3, tb = tid & 127;  // bootstrap slot, role
+    const int bi = warp / W, wr = warp % W, tb = tid % T;   // bootstrap slot, role
     BrSmem &S = reinterpret_cast<BrSmem *>(smem_raw)[bi];
     const int lane_brv = brv5(lane);
     const int n = A.keys.n;
-    const int p = w4 >> 1, h = w4 & 1;
+    const int w4 = wr & 3, p = w4 >> 1, h = wr & 1;
     const Prime pr((uint32_t)h);
 
     for (long grp = blockIdx.x; grp * B < A.count; grp += gridDim.x) {
@@ -387,7 +423,7 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
                 if (tb == 0)
                     atomicOr(A.status, err);
                 int32_t *bg = A.big + g * kBigStride;
-                for (int k = tb; k <= kN; k += 128)
+                for (int k = tb; k <= kN; k += T)
                     bg[k] = 0;
                 active = false;
             }
@@ -396,7 +432,7 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
             const int32_t *ca = A.in_a + ra * kLweStride;
             const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
             const int32_t *cc = ac ? A.in_c + rc * kLweStride : nullptr;
-            for (int i = tb; i <= n; i += 128) {
+            for (int i = tb; i <= n; i += T) {
                 uint32_t c = (uint32_t)ca[i];
                 if (A.ops) {
                     c = aa * c + ab * (uint32_t)cb[i];
@@ -408,7 +444,7 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
                 S.abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
             }
         } else {
-            for (int i = tb; i <= n; i += 128)
+            for (int i = tb; i <= n; i += T)
                 S.abar[i] = 0;
         }
         __syncthreads();
@@ -416,7 +452,7 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
         // ---- acc = (0, X^(-bbar) v)
         {
             const int m = (2 * kN - (int)S.abar[n]) & (2 * kN - 1);
-            for (int k = tb; k < kN; k += 128) {
+            for (int k = tb; k < kN; k += T) {
                 bool pos = k >= (m & (kN - 1));
                 if (m >= kN)
                     pos = !pos;
@@ -437,20 +473,34 @@ __global__ void __launch_bounds__(128 * B, 4 / B) k_blind_rotate(const BrArgs A)
                 continue;  // X^0 acc - acc = 0 for every slot: nothing changes
             const int a = S.abar[i];  // a = 0 here gives zero digits: acc unchanged
             uint32_t x[32];
-            br_digits_fwd(x, S, p, a, lane, A.keys.twb, pr);
-            __syncthreads();
-            br_pointwise(x, S, A.keys.bk_ntt + (((long)i * 2 + p) * 2 + h) * 1024, lane, pr);
-            __syncthreads();
-            br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
-            __syncthreads();
-            br_crt(S, p, h, lane);
-            __syncthreads();
+            const uint4 *bki = A.keys.bk_ntt + (((long)i * 2 + p) * 2 + h) * 1024;
+            if (W == 4) {
+                br_digits_fwd(x, S, p, a, lane, A.keys.twb, pr);
+                __syncthreads();
+                br_pointwise(x, S, bki, lane, pr);
+                __syncthreads();
+                br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
+                __syncthreads();
+                br_crt<16>(S, p, 16 * h, lane);
+                __syncthreads();
+            } else {
+                br_digit_fwd(x, S, wr >> 2, (wr >> 1) & 1, a, lane, A.keys.twb, pr);
+                __syncthreads();
+                if (wr < 4)
+                    br_pointwise(x, S, bki, lane, pr);
+                __syncthreads();
+                if (wr < 4)
+                    br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
+                __syncthreads();
+                br_crt<8>(S, wr >> 2, 8 * (wr & 3), lane);
+                __syncthreads();
+            }
         }
 
         // ---- sample extraction of coefficient 0
         if (active) {
             int32_t *bg = A.big + g * kBigStride;
-            for (int k = tb; k < kN; k += 128)
+            for (int k = tb; k < kN; k += T)
                 bg[k] = (int32_t)(k == 0 ? S.acc[0][0] : 0u - S.acc[0][kN - k]);
             if (tb == 0)
                 bg[kN] = (int32_t)S.acc[1][0];
@@ -575,26 +625,26 @@ cudaError_t launch_bk_to_ntt(const int32_t *bk_dev, uint32_t *bk_ntt, int n, con
     return cudaGetLastError();
 }
 
-template <int B>
+template <int B, int W>
 static void br_prepare()
 {
-    cudaFuncSetAttribute(k_blind_rotate<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_blind_rotate<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(B * sizeof(BrSmem)));
-    cudaFuncSetAttribute(k_blind_rotate<B>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_blind_rotate<B, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     (void)cudaGetLastError();
 }
 
-template <int B>
+template <int B, int W>
 static int br_blocks(int dev)
 {
     static int cached[64] = {0};
     if (dev < 0 || dev >= 64)
         return 1;
     if (!cached[dev]) {
-        br_prepare<B>();
+        br_prepare<B, W>();
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B>, 128 * B,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W>, 32 * W * B,
                                                           B * sizeof(BrSmem)) != cudaSuccess) {
             (void)cudaGetLastError();
             nb = 0;
@@ -609,22 +659,27 @@ int br_blocks_per_sm()
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    br_blocks<2>(dev);
-    br_blocks<4>(dev);
-    return br_blocks<1>(dev);
+    br_blocks<2, 4>(dev);
+    br_blocks<4, 4>(dev);
+    br_blocks<1, 8>(dev);
+    return br_blocks<1, 4>(dev);
 }
 
-// Lockstep group size: several bootstraps per CTA share instruction fetch
-// and key reads, but leave SMs idle when a level is narrow.
+// CTA shape: 1, 2 or 4 bootstraps per CTA in lockstep (4 warps each; groups
+// share instruction fetch and key reads but leave SMs idle when a level is
+// narrow), or kBrSplit: one bootstrap on 8 warps (shorter critical path
+// per CMux, for levels narrower than the GPU).
+static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == kBrSplit; }
+
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 {
-    if (forced == 1 || forced == 2 || forced == 4)
+    if (br_shape_ok(forced))
         return forced;
     const int t = tuned[tune_bucket(count)];
-    if (t == 1 || t == 2 || t == 4)
+    if (br_shape_ok(t))
         return t;
     const long per_sm = (count + num_sms - 1) / num_sms;
-    return per_sm >= 8 ? 4 : (per_sm >= 3 ? 2 : 1);
+    return per_sm >= 8 ? 4 : (per_sm >= 3 ? 2 : kBrSplit);
 }
 
 cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const int32_t *in_a,
@@ -655,16 +710,20 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     cudaGetDevice(&dev);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int B = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
+    const int shape = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
+    const int B = shape == kBrSplit ? 1 : shape;
     const long groups = (count + B - 1) / B;
-    long blocks_per_sm = B == 4 ? br_blocks<4>(dev) : (B == 2 ? br_blocks<2>(dev) : br_blocks<1>(dev));
+    long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)
+                       : shape == 2 ? br_blocks<2, 4>(dev)
+                       : shape == kBrSplit ? br_blocks<1, 8>(dev) : br_blocks<1, 4>(dev);
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
     const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
     (void)grid;
-    switch (B) {
-    case 4: k_blind_rotate<4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
-    case 2: k_blind_rotate<2><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
-    default: k_blind_rotate<1><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
+    switch (shape) {
+    case 4: k_blind_rotate<4, 4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
+    case 2: k_blind_rotate<2, 4><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
+    case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
+    default: k_blind_rotate<1, 4><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
     }
     return cudaGetLastError();
 }

@@ -67,12 +67,17 @@ __device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t
 #endif  // __CUDACC__
 
 // Per-context device pointers and sizes shared by the kernels.
+// Blind-rotation CTA shape code for one bootstrap spread over 8 warps (the
+// other codes, 1, 2 and 4, count 4-warp bootstraps per CTA).
+constexpr int kBrSplit = 8;
+
 struct DevKeys {
     const uint4 *bk_ntt;   // [n][2 poly][2 prime][32 reg][32 lane] x uint4(4 rows)
     const uint4 *ksk;      // [N][t][base-1][kLweStride/4] words
     const uint2 *twb;      // stage-B twiddles [2 prime][2 dir][32 reg][32 lane] (w, w')
     int n;
-    int br_group;          // bootstraps per blind-rotation CTA: 1, 2, 4, or 0 = by batch size
+    int br_group;          // blind-rotation CTA shape: 1, 2, 4 bootstraps per CTA,
+                           // kBrSplit = one bootstrap on 8 warps, 0 = by batch size
     // Autotuned launch shapes per level-width bucket (0 = not tuned): bucket b
     // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
     int8_t tune_br[8];     // bootstraps per blind-rotation CTA
