@@ -69,16 +69,141 @@ struct Prime {
     uint32_t q, q2, P;
     __device__ __forceinline__ explicit Prime(uint32_t p)
         : q(p ? kQ1 : kQ0), q2(2 * (p ? kQ1 : kQ0)), P(p) {}
+    // K q for K in {1, 2, 4, 8, 16} (16 q < 2^32 for both primes)
+    __device__ __forceinline__ uint32_t kq(int K) const
+    {
+        return K == 1 ? q : K == 2 ? q2 : K == 4 ? q2 << 1 : K == 8 ? q2 << 2 : q2 << 3;
+    }
 };
 
-// 32-point Cooley-Tukey pass in registers.
-// CYC false (stage A, negacyclic twiddles): inputs in [0, 2q); no reduction
-//   between levels, so values grow by at most 2q per level: outputs < 12q.
-// CYC true (stage D, cyclic twiddles, the first of every level is 1):
-//   Harvey's lazy butterfly, inputs and outputs in [0, 4q).
+// ---------------------------------------------------------------------
+// Lazy reductions.  Values are kept in [0, b q) with a per-element bound b
+// known at compile time; a reduction csub(x, K q) (valid for b <= 2K)
+// leaves [0, K q).  LazyPlan walks the 80 butterflies of a 32-point pass
+// in the same order as the code and places the fewest reductions that keep
+// every sum below thr q (<= 16 q < 2^32), and the final outputs below fin q:
+//  * CT butterfly (u, v) -> (u + t, u - t + K' q), t = v (trivial twiddle)
+//    or Shoup(v) in [0, 2q), K' >= bound(t) the smallest power of two;
+//  * GS butterfly (u, v) -> (u + v, d), d = u - v + K' q (K' >= bound(v)),
+//    passed on as is (trivial twiddle) or as Shoup(d) in [0, 2q).
+// The reduction is applied to the larger operand until the sum fits.
+// ---------------------------------------------------------------------
+struct LazyStep {
+    uint8_t ru[4], nru;     // csub multiples K applied to u, in order
+    uint8_t rv[4], nrv;     // ... to v (t of a trivial CT butterfly)
+    uint8_t off;            // K' of the difference
+};
+struct LazyPlan {
+    LazyStep st[5][16];     // [level][butterfly g * ln + jj]
+    uint8_t fin[32][4], nfin[32];
+    int reductions;
+    bool ok;
+};
+
+__host__ __device__ constexpr int lazy_off(int b) { return b <= 1 ? 1 : b <= 2 ? 2 : b <= 4 ? 4 : b <= 8 ? 8 : 16; }
+
+// One reduction step of a value with bound b: the smallest K in {1, 2, 4, 8}
+// with 2K >= b; returns the new bound (or b if none applies).
+__host__ __device__ constexpr int lazy_step(int b, int &K)
+{
+    K = b <= 2 ? 1 : b <= 4 ? 2 : b <= 8 ? 4 : b <= 16 ? 8 : 0;
+    if (K == 0 || K >= b)
+        return b;
+    return K > b - K ? K : b - K;
+}
+
+__host__ __device__ constexpr LazyPlan make_lazy_plan(bool ct, bool trivial_first, int in_b, int thr, int fin)
+{
+    LazyPlan P{};
+    P.ok = true;
+    int b[32] = {};
+    for (int i = 0; i < 32; ++i)
+        b[i] = in_b;
+    for (int it = 0; it < 5; ++it) {
+        const int s = ct ? it : 4 - it;
+        const int m = 1 << s, ln = 16 >> s;
+        for (int g = 0; g < m; ++g) {
+            const bool triv = trivial_first && g == 0;
+            for (int jj = 0; jj < ln; ++jj) {
+                const int j = 2 * g * ln + jj;
+                LazyStep &L = P.st[s][g * ln + jj];
+                int bu = b[j], bv = b[j + ln];
+                for (int guard = 0; guard < 8; ++guard) {
+                    const int bt = (ct && !triv) ? 2 : bv;
+                    if (bu + bt <= thr && bu + lazy_off(bt) <= 16)
+                        break;
+                    int K = 0;
+                    if ((!ct || triv) && bt >= bu) {
+                        const int nb = lazy_step(bv, K);
+                        if (nb == bv || L.nrv == 4) { P.ok = false; break; }
+                        L.rv[L.nrv++] = (uint8_t)K;
+                        bv = nb;
+                    } else {
+                        const int nb = lazy_step(bu, K);
+                        if (nb == bu || L.nru == 4) { P.ok = false; break; }
+                        L.ru[L.nru++] = (uint8_t)K;
+                        bu = nb;
+                    }
+                }
+                const int bt = (ct && !triv) ? 2 : bv;
+                L.off = (uint8_t)lazy_off(bt);
+                P.reductions += L.nru + L.nrv;
+                if (ct) {
+                    b[j] = bu + bt;
+                    b[j + ln] = bu + L.off;
+                } else {
+                    b[j] = bu + bv;
+                    b[j + ln] = triv ? bu + L.off : 2;
+                }
+                if (b[j] > 16 || b[j + ln] > 16)
+                    P.ok = false;
+            }
+        }
+    }
+    for (int i = 0; i < 32; ++i) {
+        while (b[i] > fin) {
+            int K = 0;
+            const int nb = lazy_step(b[i], K);
+            if (nb == b[i] || P.nfin[i] == 4) { P.ok = false; break; }
+            P.fin[i][P.nfin[i]++] = (uint8_t)K;
+            b[i] = nb;
+        }
+        P.reductions += P.nfin[i];
+    }
+    return P;
+}
+
+// Forward passes: stage A (negacyclic twiddles, inputs [0, 2q), outputs
+// < 12q, no reduction needed) and stage D (cyclic, the first twiddle of
+// every level is 1; inputs [0, 2q), outputs [0, 4q) for the pointwise
+// products).  Inverse passes: stage D' (cyclic GS, inputs [0, 2q) from the
+// pointwise Montgomery step, outputs < 16q into the Shoup twiddle) and
+// stage A' (negacyclic GS, inputs [0, 2q), outputs [0, 2q)).
+constexpr LazyPlan kPlanFwdA = make_lazy_plan(true, false, 2, 12, 16);
+constexpr LazyPlan kPlanFwdD = make_lazy_plan(true, true, 2, 8, 4);
+constexpr LazyPlan kPlanInvD = make_lazy_plan(false, true, 2, 16, 16);
+constexpr LazyPlan kPlanInvA = make_lazy_plan(false, false, 2, 16, 2);
+static_assert(kPlanFwdA.ok && kPlanFwdD.ok && kPlanInvD.ok && kPlanInvA.ok, "lazy plan");
+static_assert(kPlanFwdA.reductions == 0 && kPlanFwdD.reductions == 65 &&
+              kPlanInvD.reductions == 14 && kPlanInvA.reductions == 36, "lazy plan size");
+
+__device__ __forceinline__ uint32_t lazy_reduce_n(uint32_t x, const uint8_t (&ks)[4], int n,
+                                                  const Prime &pr)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < n)
+            x = csub(x, pr.kq(ks[k]));
+    return x;
+}
+
+// 32-point Cooley-Tukey pass in registers (CYC false: stage A, negacyclic
+// twiddles; CYC true: stage D, cyclic twiddles), reductions by plan.
 template <bool CYC>
 __device__ __forceinline__ void ct32(uint32_t (&x)[32], const Prime &pr)
 {
+    constexpr LazyPlan PL = CYC ? make_lazy_plan(true, true, 2, 8, 4)
+                                : make_lazy_plan(true, false, 2, 12, 16);
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int m = 1 << s, ln = 16 >> s;
@@ -90,21 +215,27 @@ __device__ __forceinline__ void ct32(uint32_t (&x)[32], const Prime &pr)
 #pragma unroll
             for (int jj = 0; jj < ln; ++jj) {
                 const int j = 2 * g * ln + jj;
-                const uint32_t u = CYC ? csub(x[j], pr.q2) : x[j];
-                const uint32_t t = (CYC && g == 0) ? csub(x[j + ln], pr.q2)
+                const LazyStep &L = PL.st[s][g * ln + jj];
+                const uint32_t u = lazy_reduce_n(x[j], L.ru, L.nru, pr);
+                const uint32_t t = (CYC && g == 0) ? lazy_reduce_n(x[j + ln], L.rv, L.nrv, pr)
                                                    : mul_shoup(x[j + ln], w, wp, pr.q);
                 x[j] = u + t;
-                x[j + ln] = u - t + pr.q2;
+                x[j + ln] = u - t + pr.kq(L.off);
             }
         }
     }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        x[r] = lazy_reduce_n(x[r], PL.fin[r], PL.nfin[r], pr);
 }
 
-// Inverse (Gentleman-Sande) of ct32, inputs and outputs in [0, 2q); the
-// result is 32 times the inverse transform.
+// Inverse (Gentleman-Sande) of ct32, reductions by plan; the result is 32
+// times the inverse transform.
 template <bool CYC>
 __device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 {
+    constexpr LazyPlan PL = CYC ? make_lazy_plan(false, true, 2, 16, 16)
+                                : make_lazy_plan(false, false, 2, 16, 2);
 #pragma unroll
     for (int s = 4; s >= 0; --s) {
         const int m = 1 << s, ln = 16 >> s;
@@ -116,13 +247,18 @@ __device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 #pragma unroll
             for (int jj = 0; jj < ln; ++jj) {
                 const int j = 2 * g * ln + jj;
-                const uint32_t u = x[j], v = x[j + ln];
-                x[j] = csub(u + v, pr.q2);
-                const uint32_t d = u - v + pr.q2;
-                x[j + ln] = (CYC && g == 0) ? csub(d, pr.q2) : mul_shoup(d, w, wp, pr.q);
+                const LazyStep &L = PL.st[s][g * ln + jj];
+                const uint32_t u = lazy_reduce_n(x[j], L.ru, L.nru, pr);
+                const uint32_t v = lazy_reduce_n(x[j + ln], L.rv, L.nrv, pr);
+                x[j] = u + v;
+                const uint32_t d = u - v + pr.kq(L.off);
+                x[j + ln] = (CYC && g == 0) ? d : mul_shoup(d, w, wp, pr.q);
             }
         }
     }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        x[r] = lazy_reduce_n(x[r], PL.fin[r], PL.nfin[r], pr);
 }
 
 // Forward negacyclic NTT of one polynomial held by one warp.
@@ -385,7 +521,8 @@ __device__ __forceinline__ bool gate_consts(int op, uint32_t &mu, uint32_t &aa, 
 //          0..3 run phases 2-3 as (p, h); every warp runs phase 4 on a
 //          quarter of polynomial w >> 2.
 template <int B, int W>
-__global__ void __launch_bounds__(32 * W * B, 16 / (W * B)) k_blind_rotate(const BrArgs A)
+__global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 / (W * B))
+    k_blind_rotate(const BrArgs A)
 {
     constexpr int T = 32 * W;      // threads per bootstrap
     extern __shared__ uint4 smem_raw[];
@@ -662,6 +799,7 @@ int br_blocks_per_sm()
     br_blocks<2, 4>(dev);
     br_blocks<4, 4>(dev);
     br_blocks<1, 8>(dev);
+    br_blocks<5, 4>(dev);
     return br_blocks<1, 4>(dev);
 }
 
@@ -669,7 +807,7 @@ int br_blocks_per_sm()
 // share instruction fetch and key reads but leave SMs idle when a level is
 // narrow), or kBrSplit: one bootstrap on 8 warps (shorter critical path
 // per CMux, for levels narrower than the GPU).
-static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == kBrSplit; }
+static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 5 || v == kBrSplit; }
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 {
@@ -713,13 +851,15 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     const int shape = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
     const int B = shape == kBrSplit ? 1 : shape;
     const long groups = (count + B - 1) / B;
-    long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)
+    long blocks_per_sm = shape == 5 ? br_blocks<5, 4>(dev)
+                       : shape == 4 ? br_blocks<4, 4>(dev)
                        : shape == 2 ? br_blocks<2, 4>(dev)
                        : shape == kBrSplit ? br_blocks<1, 8>(dev) : br_blocks<1, 4>(dev);
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
     const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
     (void)grid;
     switch (shape) {
+    case 5: k_blind_rotate<5, 4><<<blocks, 640, 5 * sizeof(BrSmem), stream>>>(A); break;
     case 4: k_blind_rotate<4, 4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
     case 2: k_blind_rotate<2, 4><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
     case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
