@@ -799,7 +799,6 @@ int br_blocks_per_sm()
     br_blocks<2, 4>(dev);
     br_blocks<4, 4>(dev);
     br_blocks<1, 8>(dev);
-    br_blocks<5, 4>(dev);
     return br_blocks<1, 4>(dev);
 }
 
@@ -807,7 +806,7 @@ int br_blocks_per_sm()
 // share instruction fetch and key reads but leave SMs idle when a level is
 // narrow), or kBrSplit: one bootstrap on 8 warps (shorter critical path
 // per CMux, for levels narrower than the GPU).
-static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 5 || v == kBrSplit; }
+static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == kBrSplit; }
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 {
@@ -851,15 +850,13 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     const int shape = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
     const int B = shape == kBrSplit ? 1 : shape;
     const long groups = (count + B - 1) / B;
-    long blocks_per_sm = shape == 5 ? br_blocks<5, 4>(dev)
-                       : shape == 4 ? br_blocks<4, 4>(dev)
+    long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)
                        : shape == 2 ? br_blocks<2, 4>(dev)
                        : shape == kBrSplit ? br_blocks<1, 8>(dev) : br_blocks<1, 4>(dev);
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
     const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
     (void)grid;
     switch (shape) {
-    case 5: k_blind_rotate<5, 4><<<blocks, 640, 5 * sizeof(BrSmem), stream>>>(A); break;
     case 4: k_blind_rotate<4, 4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
     case 2: k_blind_rotate<2, 4><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
     case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
