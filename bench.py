@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--cpu-gates", type=int, default=128)
     ap.add_argument("--br-only", type=int, default=0, help="profile mode: blind rotation alone")
     ap.add_argument("--br-group", type=int, default=0, help="blind-rotation CTA shape: 1, 2, 4 bootstraps per CTA, 8 = one "
-                         "bootstrap on 8 warps (0: automatic)")
+                         "bootstrap on 8 warps, 16 = one bootstrap on two CTAs (0: automatic)")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson requests at 3 rates (config 4)")
     ap.add_argument("--serve-requests", type=int, default=10000)

@@ -34,7 +34,11 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tgb {
 
@@ -411,12 +415,10 @@ __device__ __forceinline__ void br_digits_fwd(uint32_t (&x)[32], BrSmem &S, int 
 // polynomial j of TLWE polynomial c of X^a acc - acc and transforms it
 // modulo prime h into S.fwd[2c + j][h] (its own slot, also the transpose
 // scratch).
-__device__ __forceinline__ void br_digit_fwd(uint32_t (&x)[32], BrSmem &S, int c, int j, int a,
-                                             int lane, const uint2 *__restrict__ twb,
-                                             const Prime &pr)
+__device__ __forceinline__ void digit_fwd(uint32_t (&x)[32], const uint32_t *ac, uint32_t *sj,
+                                          int j, int a, int lane, const uint2 *__restrict__ twb,
+                                          const Prime &pr)
 {
-    const uint32_t *ac = S.acc[c];
-    uint32_t *sj = S.fwd[2 * c + j][pr.P];
     const int shift = j ? 12 : 22;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
@@ -431,6 +433,13 @@ __device__ __forceinline__ void br_digit_fwd(uint32_t (&x)[32], BrSmem &S, int c
 #pragma unroll
     for (int r = 0; r < 32; ++r)
         sj[r * 32 + lane] = x[r];
+}
+
+__device__ __forceinline__ void br_digit_fwd(uint32_t (&x)[32], BrSmem &S, int c, int j, int a,
+                                             int lane, const uint2 *__restrict__ twb,
+                                             const Prime &pr)
+{
+    digit_fwd(x, S.acc[c], S.fwd[2 * c + j][pr.P], j, a, lane, twb, pr);
 }
 
 // Phase 2: pointwise products for output polynomial p modulo prime h,
@@ -475,19 +484,24 @@ __device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4,
 // the centring decision (v >= q0 q1 / 2) is exactly u > (q1 - 1) / 2.
 // The calling warp lifts registers r0 .. r0 + NR - 1 of polynomial p.
 template <int NR>
-__device__ __forceinline__ void br_crt(BrSmem &S, int p, int r0, int lane)
+__device__ __forceinline__ void crt_rows(uint32_t *acc, const uint32_t *x0, const uint32_t *x1,
+                                         int r0, int lane)
 {
-    const uint32_t *x0 = S.fwd[p * 2 + 0][1], *x1 = S.fwd[p * 2 + 1][1];
     const uint32_t c = c_ntt.crt_c, cp = c_ntt.crt_cp, plo = c_ntt.p_lo;
     constexpr uint32_t uh = (kQ1 - 1) / 2;
-    uint32_t *acc = S.acc[p];
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) {
         const int e = (r0 + rr) * 32 + lane;
-        const uint32_t r0 = x0[e], r1 = x1[e];
-        const uint32_t u = csub(mul_shoup(r1 - r0 + 2 * kQ1, c, cp, kQ1), kQ1);
-        acc[e] += r0 + kQ0 * u - (u > uh ? plo : 0u);
+        const uint32_t v0 = x0[e], v1 = x1[e];
+        const uint32_t u = csub(mul_shoup(v1 - v0 + 2 * kQ1, c, cp, kQ1), kQ1);
+        acc[e] += v0 + kQ0 * u - (u > uh ? plo : 0u);
     }
+}
+
+template <int NR>
+__device__ __forceinline__ void br_crt(BrSmem &S, int p, int r0, int lane)
+{
+    crt_rows<NR>(S.acc[p], S.fwd[p * 2 + 0][1], S.fwd[p * 2 + 1][1], r0, lane);
 }
 
 // Linear part of gate `op`: c = mu + aa ca + ab cb + ac cc.  Returns false
@@ -510,6 +524,93 @@ __device__ __forceinline__ bool gate_consts(int op, uint32_t &mu, uint32_t &aa, 
     case TFHE_ORYN:  mu = kMu;           aa = 1u; ab = 0u - 1u; return true;
     default:         mu = 0u;            aa = ab = 0u;      return false;
     }
+}
+
+// Gate combine + mod switch (the fused prologue) of gate slot g into
+// abar[0..n] by the T threads of one bootstrap.  An empty slot (g >= count)
+// or a bad one runs with abar = 0; a bad slot (opcode without its inputs,
+// gather index out of range) is flagged in the status word and, when
+// `writer`, its output row is zeroed.  Returns whether the slot is active.
+template <int T>
+__device__ __forceinline__ bool br_prologue(const BrArgs &A, long g, int tb, uint16_t *abar,
+                                            bool writer)
+{
+    const int n = A.keys.n;
+    bool active = g < A.count;
+    long ra = 0, rb = 0, rc = -1;
+    uint32_t mu_g = 0, aa = 1, ab = 0, ac = 0;
+    if (active) {
+        uint32_t err = 0;
+        if (A.ops && !gate_consts(A.ops[g], mu_g, aa, ab, ac))
+            err = kErrOpcode;
+        ra = A.idx_a ? (long)A.idx_a[g] : g;
+        rb = A.ops ? (A.idx_b ? (long)A.idx_b[g] : g) : 0;
+        if (ac) {
+            if (!A.in_c)
+                err |= kErrOpcode;
+            else
+                rc = A.idx_c ? (long)A.idx_c[g] : g;
+        }
+        if (!(ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b)) &&
+              (!ac || !A.in_c || (rc >= 0 && rc < A.rows_c))))
+            err |= kErrGather;
+        if (err) {
+            if (writer) {
+                if (tb == 0)
+                    atomicOr(A.status, err);
+                int32_t *bg = A.big + g * kBigStride;
+                for (int k = tb; k <= kN; k += T)
+                    bg[k] = 0;
+            }
+            active = false;
+        }
+    }
+    if (active) {
+        const int32_t *ca = A.in_a + ra * kLweStride;
+        const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
+        const int32_t *cc = ac ? A.in_c + rc * kLweStride : nullptr;
+        for (int i = tb; i <= n; i += T) {
+            uint32_t c = (uint32_t)ca[i];
+            if (A.ops) {
+                c = aa * c + ab * (uint32_t)cb[i];
+                if (ac)
+                    c += ac * (uint32_t)cc[i];
+            }
+            if (i == n)
+                c += mu_g;
+            abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
+        }
+    } else {
+        for (int i = tb; i <= n; i += T)
+            abar[i] = 0;
+    }
+    return active;
+}
+
+// acc = (0, X^(-bbar) v), v = mu (1 + X + ... + X^(N-1)).
+template <int T>
+__device__ __forceinline__ void br_acc_init(const BrArgs &A, uint32_t (*acc)[kN], int bbar, int tb)
+{
+    const int m = (2 * kN - bbar) & (2 * kN - 1);
+    for (int k = tb; k < kN; k += T) {
+        bool pos = k >= (m & (kN - 1));
+        if (m >= kN)
+            pos = !pos;
+        acc[0][k] = 0u;
+        acc[1][k] = pos ? A.mu : 0u - A.mu;
+    }
+}
+
+// Sample extraction of coefficient 0: a'_0 = a_0, a'_j = -a_(N-j), b' = b_0.
+template <int T>
+__device__ __forceinline__ void br_extract(const BrArgs &A, long g, const uint32_t (*acc)[kN],
+                                           int tb)
+{
+    int32_t *bg = A.big + g * kBigStride;
+    for (int k = tb; k < kN; k += T)
+        bg[k] = (int32_t)(k == 0 ? acc[0][0] : 0u - acc[0][kN - k]);
+    if (tb == 0)
+        bg[kN] = (int32_t)acc[1][0];
 }
 
 // B bootstraps per CTA, W warps each (W = 4: B in {1, 2, 4} in lockstep;
@@ -536,67 +637,9 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
 
     for (long grp = blockIdx.x; grp * B < A.count; grp += gridDim.x) {
         const long g = grp * B + bi;
-        // ---- gate combine + mod switch (fused prologue); an empty or bad
-        // slot runs with abar = 0 and writes nothing (bad: zero row + flag)
-        bool active = g < A.count;
-        long ra = 0, rb = 0, rc = -1;
-        uint32_t mu_g = 0, aa = 1, ab = 0, ac = 0;
-        if (active) {
-            uint32_t err = 0;
-            if (A.ops && !gate_consts(A.ops[g], mu_g, aa, ab, ac))
-                err = kErrOpcode;
-            ra = A.idx_a ? (long)A.idx_a[g] : g;
-            rb = A.ops ? (A.idx_b ? (long)A.idx_b[g] : g) : 0;
-            if (ac) {
-                if (!A.in_c)
-                    err |= kErrOpcode;
-                else
-                    rc = A.idx_c ? (long)A.idx_c[g] : g;
-            }
-            if (!(ra >= 0 && ra < A.rows_a && (!A.ops || (rb >= 0 && rb < A.rows_b)) &&
-                  (!ac || !A.in_c || (rc >= 0 && rc < A.rows_c))))
-                err |= kErrGather;
-            if (err) {
-                if (tb == 0)
-                    atomicOr(A.status, err);
-                int32_t *bg = A.big + g * kBigStride;
-                for (int k = tb; k <= kN; k += T)
-                    bg[k] = 0;
-                active = false;
-            }
-        }
-        if (active) {
-            const int32_t *ca = A.in_a + ra * kLweStride;
-            const int32_t *cb = A.ops ? A.in_b + rb * kLweStride : nullptr;
-            const int32_t *cc = ac ? A.in_c + rc * kLweStride : nullptr;
-            for (int i = tb; i <= n; i += T) {
-                uint32_t c = (uint32_t)ca[i];
-                if (A.ops) {
-                    c = aa * c + ab * (uint32_t)cb[i];
-                    if (ac)
-                        c += ac * (uint32_t)cc[i];
-                }
-                if (i == n)
-                    c += mu_g;
-                S.abar[i] = (uint16_t)(((c + (1u << 20)) >> 21) & (2 * kN - 1));
-            }
-        } else {
-            for (int i = tb; i <= n; i += T)
-                S.abar[i] = 0;
-        }
+        const bool active = br_prologue<T>(A, g, tb, S.abar, true);
         __syncthreads();
-
-        // ---- acc = (0, X^(-bbar) v)
-        {
-            const int m = (2 * kN - (int)S.abar[n]) & (2 * kN - 1);
-            for (int k = tb; k < kN; k += T) {
-                bool pos = k >= (m & (kN - 1));
-                if (m >= kN)
-                    pos = !pos;
-                S.acc[0][k] = 0u;
-                S.acc[1][k] = pos ? A.mu : 0u - A.mu;
-            }
-        }
+        br_acc_init<T>(A, S.acc, S.abar[n], tb);
         __syncthreads();
 
         // ---- n CMux steps, all B bootstraps in lockstep
@@ -634,16 +677,112 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
             }
         }
 
-        // ---- sample extraction of coefficient 0
-        if (active) {
-            int32_t *bg = A.big + g * kBigStride;
-            for (int k = tb; k < kN; k += T)
-                bg[k] = (int32_t)(k == 0 ? S.acc[0][0] : 0u - S.acc[0][kN - k]);
-            if (tb == 0)
-                bg[kN] = (int32_t)S.acc[1][0];
-        }
+        if (active)
+            br_extract<T>(A, g, S.acc, tb);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------
+// One bootstrap on a cluster of two CTAs (two SMs): CTA h works modulo
+// prime h for the whole CMux and the two exchange their inverse-transform
+// residues through distributed shared memory for the CRT.  For levels
+// narrower than the GPU, where the per-CMux critical path sets the time.
+// ---------------------------------------------------------------------
+
+struct PairSmem {
+    uint32_t acc[2][kN];        // TLWE accumulator (the same in both CTAs)
+    uint32_t fwd[4][kSlot];     // digit rows modulo this CTA's prime; transpose scratch
+    uint32_t pw[2][kN];         // pointwise products [p][reg*32+lane], [0, 2q)
+    uint32_t res[2][2][kN];     // published residues [buffer][p][reg*32+lane], [0, q)
+    uint16_t abar[kLweStride];
+};
+
+// Pointwise products of rows r0 .. r0 + 15 of output polynomial p.
+__device__ __forceinline__ void pair_pointwise(PairSmem &S, const uint4 *__restrict__ bkp, int p,
+                                               int r0, int lane, const Prime &pr)
+{
+    const uint32_t qn = c_ntt.q_inv[pr.P];
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+        const int e = (r0 + rr) * 32 + lane;
+        const uint4 b = __ldg(bkp + e);
+        uint64_t s = (uint64_t)S.fwd[0][e] * b.x;
+        s += (uint64_t)S.fwd[1][e] * b.y;
+        s += (uint64_t)S.fwd[2][e] * b.z;
+        s += (uint64_t)S.fwd[3][e] * b.w;
+        S.pw[p][e] = mont_reduce(s, pr.q, qn);
+    }
+}
+
+// 8 warps per CTA.  Per CMux: warps (c, j) < 4 form and transform digit j
+// of polynomial c; warps (p, half) < 4 the pointwise products of half of
+// output polynomial p; warps p < 2 the inverse transform of p, published to
+// a residue buffer; then, after a cluster barrier, all 8 warps lift a
+// quarter of one polynomial each, reading the partner's residues remotely.
+// Both CTAs hold and update the whole accumulator, so the only exchange is
+// the residues.  The residue buffers alternate by executed CMux: a buffer
+// is rewritten two CMux steps after the partner read it, with the partner's
+// barrier arrival of the step between in between.  Control flow is the
+// same in both CTAs of a cluster (same gate, same abar), so every cluster
+// barrier is reached by both.
+__global__ void __launch_bounds__(256, 1) k_blind_rotate_pair(const BrArgs A)
+{
+    extern __shared__ uint4 smem_raw[];
+    PairSmem &S = *reinterpret_cast<PairSmem *>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lane_brv = brv5(lane);
+    const int n = A.keys.n;
+    const Prime pr((uint32_t)rank);
+    const long nclusters = gridDim.x / 2, cid = blockIdx.x / 2;
+    int par = 0;
+    for (long g = cid; g < A.count; g += nclusters) {
+        const bool active = br_prologue<256>(A, g, tid, S.abar, rank == 0);
+        __syncthreads();
+        br_acc_init<256>(A, S.acc, S.abar[n], tid);
+        __syncthreads();
+        for (int i = 0; i < n; ++i) {
+            const int a = S.abar[i];
+            if (a == 0)
+                continue;   // X^0 acc - acc = 0: nothing changes (in both CTAs)
+            uint32_t x[32];
+            if (warp < 4)
+                digit_fwd(x, S.acc[warp >> 1], S.fwd[warp], warp & 1, a, lane, A.keys.twb, pr);
+            __syncthreads();
+            if (warp < 4) {
+                const int p = warp >> 1;
+                pair_pointwise(S, A.keys.bk_ntt + (((long)i * 2 + p) * 2 + rank) * 1024, p,
+                               16 * (warp & 1), lane, pr);
+            }
+            __syncthreads();
+            if (warp < 2) {
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    x[r] = S.pw[warp][r * 32 + lane];
+                inv_ntt(x, S.fwd[warp], lane, lane_brv, A.keys.twb, pr);
+                uint32_t *out = S.res[par][warp];
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    out[r * 32 + lane] = csub(x[r], pr.q);
+            }
+            cl.sync();
+            {
+                const int p = warp >> 2;
+                const uint32_t *mine = S.res[par][p];
+                const uint32_t *other = cl.map_shared_rank(mine, rank ^ 1);
+                crt_rows<8>(S.acc[p], rank == 0 ? mine : other, rank == 0 ? other : mine,
+                            8 * (warp & 3), lane);
+            }
+            par ^= 1;
+            __syncthreads();
+        }
+        if (active && rank == 0)
+            br_extract<256>(A, g, S.acc, tid);
+        __syncthreads();
+    }
+    cl.sync();   // the partner may still read this CTA's residues
 }
 
 // ---------------------------------------------------------------------
@@ -806,7 +945,10 @@ int br_blocks_per_sm()
 // share instruction fetch and key reads but leave SMs idle when a level is
 // narrow), or kBrSplit: one bootstrap on 8 warps (shorter critical path
 // per CMux, for levels narrower than the GPU).
-static bool br_shape_ok(int v) { return v == 1 || v == 2 || v == 4 || v == kBrSplit; }
+static bool br_shape_ok(int v)
+{
+    return v == 1 || v == 2 || v == 4 || v == kBrSplit || v == kBrPair;
+}
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
 {
@@ -848,6 +990,30 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int shape = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
+    if (shape == kBrPair) {
+        static int prepared[64] = {0};
+        if (dev >= 0 && dev < 64 && !prepared[dev]) {
+            cudaFuncSetAttribute(k_blind_rotate_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PairSmem));
+            (void)cudaGetLastError();
+            prepared[dev] = 1;
+        }
+        const long pairs = sms >= 2 ? sms / 2 : 1;   // one CTA per SM
+        const long clusters = count < pairs ? count : pairs;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sizeof(PairSmem);
+        cfg.stream = stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_blind_rotate_pair, A);
+    }
     const int B = shape == kBrSplit ? 1 : shape;
     const long groups = (count + B - 1) / B;
     long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)

@@ -67,9 +67,11 @@ __device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t
 #endif  // __CUDACC__
 
 // Per-context device pointers and sizes shared by the kernels.
-// Blind-rotation CTA shape code for one bootstrap spread over 8 warps (the
-// other codes, 1, 2 and 4, count 4-warp bootstraps per CTA).
+// Blind-rotation CTA shape codes: one bootstrap spread over 8 warps, and
+// one bootstrap on a cluster of two CTAs (one prime each).  The other
+// codes, 1, 2 and 4, count 4-warp bootstraps per CTA.
 constexpr int kBrSplit = 8;
+constexpr int kBrPair = 16;
 
 struct DevKeys {
     const uint4 *bk_ntt;   // [n][2 poly][2 prime][32 reg][32 lane] x uint4(4 rows)
@@ -77,7 +79,8 @@ struct DevKeys {
     const uint2 *twb;      // stage-B twiddles [2 prime][2 dir][32 reg][32 lane] (w, w')
     int n;
     int br_group;          // blind-rotation CTA shape: 1, 2, 4 bootstraps per CTA,
-                           // kBrSplit = one bootstrap on 8 warps, 0 = by batch size
+                           // kBrSplit = one bootstrap on 8 warps, kBrPair = one
+                           // bootstrap on two CTAs, 0 = tuned or by batch size
     // Autotuned launch shapes per level-width bucket (0 = not tuned): bucket b
     // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
     int8_t tune_br[8];     // bootstraps per blind-rotation CTA

@@ -1,6 +1,7 @@
 // tune.cu -- autotuner for the launch shapes of the two bootstrapping
 // kernels: the blind-rotation CTA shape (1, 2 or 4 bootstraps per CTA in
-// lockstep, or one bootstrap spread over 8 warps) and the
+// lockstep, one bootstrap spread over 8 warps, or one bootstrap on a
+// cluster of two CTAs) and the
 // key switch's j-split (1 .. 32 chunks), chosen per level-width bucket by
 // timing the candidates on synthetic ciphertexts with the context's keys.
 // Results can be cached in a small text file keyed by device name and SM
@@ -120,7 +121,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
         for (int b = 0; b < 8 && e == cudaSuccess; ++b) {
             const long W = widths[b];
             float best = 1e30f;
-            for (int B : {1, 2, 4, kBrSplit}) {
+            for (int B : {1, 2, 4, kBrSplit, kBrPair}) {
                 K.br_group = B;
                 float tot = 0;
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {

@@ -179,11 +179,12 @@ def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
     assert np.array_equal(got[sample, :p.n + 1], want)
 
 
-@pytest.mark.parametrize("group", [1, 2, 4, 8])
+@pytest.mark.parametrize("group", [1, 2, 4, 8, 16])
 def test_each_lockstep_group_bit_exact(gpu, orc, group):
     """Blind rotation with 1, 2 or 4 bootstraps per CTA (13 gates leave empty
-    slots in the last group, and skipped CMux steps in some slots), and with
-    one bootstrap spread over 8 warps (shape 8)."""
+    slots in the last group, and skipped CMux steps in some slots), with one
+    bootstrap spread over 8 warps (shape 8), and with one bootstrap on a
+    cluster of two CTAs exchanging residues (shape 16)."""
     torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
     count = 13
     bits, cts, dev = _fresh(gpu, orc, count, 40 + group, f"grp{group}", zero_some=True)
@@ -209,7 +210,7 @@ def test_autotune_keeps_results(gpu, orc):
     after = torch.zeros_like(before)
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], before)
     choices = gpu["ctx"].autotune()
-    assert set(choices["br_group"].values()) <= {1, 2, 4, 8}
+    assert set(choices["br_group"].values()) <= {1, 2, 4, 8, 16}
     assert set(choices["ks_chunks"].values()) <= {1, 2, 4, 8, 16, 32}
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], after)
     assert torch.equal(before, after)
