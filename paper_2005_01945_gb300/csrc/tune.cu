@@ -122,6 +122,10 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
             const long W = widths[b];
             float best = 1e30f;
             for (int B : {1, 2, 4, kBrSplit, kBrPair}) {
+                // the latency shapes hold one bootstrap per SM (or SM pair):
+                // only candidates while a level fits in about one wave of them
+                if ((B == kBrSplit || B == kBrPair) && W > 2L * ctx->num_sms)
+                    continue;
                 K.br_group = B;
                 float tot = 0;
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
