@@ -247,21 +247,25 @@ typedef enum {
                              /*    SMs, one prime each; lowest latency), or 0       */
                              /*    (default): autotuned, else by batch size         */
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
-    TFHE_OPT_LEVEL_WIDTH = 5 /* target gates per level for BALANCED (0: one wave,   */
+    TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave,   */
                              /*    4 bootstraps per SM)                             */
+    TFHE_OPT_KS_KERNEL = 6   /* key-switch kernel: 64 = tiled (64 gates per CTA, key */
+                             /*    rows staged in shared memory by bulk copies),    */
+                             /*    1, 2, 4, .. 32 = direct kernel with that j-split, */
+                             /*    or 0 (default): autotuned, else by batch size    */
 } tfhe_option;
 
 int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);
 
 /* Autotune the launch shapes of the two bootstrapping kernels for this
  * context's device: for each level-width bucket (<= 152, 304, 608, 1216,
- * 2432, 4864, 9728 gates, and more) time 1, 2 and 4 bootstraps per
- * blind-rotation CTA and 1..32 key-switch j-chunks on synthetic
- * ciphertexts, and keep the fastest (a few seconds; results never change).
- * cache_path (may be NULL): a text file consulted first and appended to
- * after tuning, keyed by device name and SM count.  choices (may be NULL)
- * receives 16 ints: the 8 blind-rotation group sizes, then the 8 key-switch
- * chunk counts.  Synchronous. */
+ * 2432, 4864, 9728 gates, and more) time the blind-rotation CTA shapes
+ * (TFHE_OPT_BR_GROUP values) and the key-switch kernels (TFHE_OPT_KS_KERNEL
+ * values) on synthetic ciphertexts, and keep the fastest (a few seconds;
+ * results never change).  cache_path (may be NULL): a text file consulted
+ * first and appended to after tuning, keyed by device name and SM count.
+ * choices (may be NULL) receives 16 ints: the 8 blind-rotation shapes, then
+ * the 8 key-switch choices.  Synchronous. */
 int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t *choices);
 
 /* Kernel launches the context has issued so far (kernels inside a replayed

@@ -99,7 +99,9 @@ EXPORTS = {
 }
 
 GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA = range(9)
-OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH = range(6)
+OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH, \
+    OPT_KS_KERNEL = range(7)
+KS_TILED = 64   # OPT_KS_KERNEL value of the tiled key-switch kernel
 SCHED_ASAP, SCHED_BALANCED = 0, 1
 
 

@@ -94,10 +94,10 @@ int run_bootstrap(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "blind rotation launch");
     e = launch_keyswitch(ctx->keys.ksk, ctx->big, out, idx_out, rows_out, count, ctx->prm.n,
-                         ctx->num_sms, ctx->status, stream, ctx->keys.tune_ks);
+                         ctx->num_sms, ctx->status, stream, &ctx->keys);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "key switch launch");
-    ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms, ctx->keys.tune_ks);
+    ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms, &ctx->keys);
     return TFHE_OK;
 }
 
@@ -303,10 +303,10 @@ int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count
     DeviceGuard dg(ctx->device);
     cudaError_t e = launch_keyswitch(ctx->keys.ksk, big, out, nullptr, (long)count, (long)count,
                                      ctx->prm.n, ctx->num_sms, ctx->status, (cudaStream_t)stream,
-                                     ctx->keys.tune_ks);
+                                     &ctx->keys);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "key switch launch");
-    ctx->launches += keyswitch_kernels((long)count, ctx->num_sms, ctx->keys.tune_ks);
+    ctx->launches += keyswitch_kernels((long)count, ctx->num_sms, &ctx->keys);
     return TFHE_OK;
 }
 

@@ -806,12 +806,12 @@ static cudaError_t enqueue_levels(tfhe_ctx *ctx, Plan &P, cudaStream_t st, bool 
             e = mark(3 * (l - 1) + 1);
         if (e == cudaSuccess)
             e = launch_keyswitch(ctx->keys.ksk, P.big, P.pool, P.d_io + off, P.pool_rows, cnt,
-                                 ctx->prm.n, ctx->num_sms, ctx->status, st, ctx->keys.tune_ks);
+                                 ctx->prm.n, ctx->num_sms, ctx->status, st, &ctx->keys);
         if (e == cudaSuccess)
             e = mark(3 * (l - 1) + 2);
         if (e != cudaSuccess)
             return e;
-        kernels += 1 + keyswitch_kernels(cnt, ctx->num_sms, ctx->keys.tune_ks);
+        kernels += 1 + keyswitch_kernels(cnt, ctx->num_sms, &ctx->keys);
     }
     P.kernels_per_run = kernels;
     return cudaSuccess;
@@ -829,10 +829,10 @@ static cudaError_t enqueue_per_gate(tfhe_ctx *ctx, Plan &P, cudaStream_t st)
         if (e != cudaSuccess)
             return e;
         e = launch_keyswitch(ctx->keys.ksk, P.big, P.pool, P.d_io + k, P.pool_rows, 1, ctx->prm.n,
-                             ctx->num_sms, ctx->status, st, ctx->keys.tune_ks);
+                             ctx->num_sms, ctx->status, st, &ctx->keys);
         if (e != cudaSuccess)
             return e;
-        ctx->launches += 1 + keyswitch_kernels(1, ctx->num_sms, ctx->keys.tune_ks);
+        ctx->launches += 1 + keyswitch_kernels(1, ctx->num_sms, &ctx->keys);
     }
     return cudaSuccess;
 }
@@ -1052,6 +1052,13 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
             return fail(ctx, TFHE_EINVAL, "TFHE_OPT_LEVEL_WIDTH must be >= 0");
         C.level_width = (long)value;
         return TFHE_OK;
+    case TFHE_OPT_KS_KERNEL:
+        if (value != 0 && value != kKsTiled &&
+            !(value >= 1 && value <= 32 && (value & (value - 1)) == 0))
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_KS_KERNEL must be 0, 64 or 1, 2, 4, .. 32");
+        ctx->keys.ks_kernel = (int)value;
+        invalidate_graphs(ctx);   // captured graphs hold the old launch shape
+        return TFHE_OK;
     case TFHE_OPT_BR_GROUP:
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != kBrSplit &&
             value != kBrPair)
@@ -1091,7 +1098,7 @@ int tfhe_ctx_profile(tfhe_ctx *ctx, double *br_ms, int64_t *br_launches, int64_t
             kt += b;
             bl += 1;
             bb += cnt;
-            kl += keyswitch_kernels(cnt, ctx->num_sms, ctx->keys.tune_ks);
+            kl += keyswitch_kernels(cnt, ctx->num_sms, &ctx->keys);
         }
     }
     C.profiled.clear();

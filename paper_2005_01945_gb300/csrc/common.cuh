@@ -72,6 +72,9 @@ __device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t
 // codes, 1, 2 and 4, count 4-warp bootstraps per CTA.
 constexpr int kBrSplit = 8;
 constexpr int kBrPair = 16;
+// Key-switch launch code for the tiled kernel (shared-memory key stages);
+// the codes 1 .. 32 are j-chunks of the direct kernel.
+constexpr int kKsTiled = 64;
 
 struct DevKeys {
     const uint4 *bk_ntt;   // [n][2 poly][2 prime][32 reg][32 lane] x uint4(4 rows)
@@ -81,10 +84,12 @@ struct DevKeys {
     int br_group;          // blind-rotation CTA shape: 1, 2, 4 bootstraps per CTA,
                            // kBrSplit = one bootstrap on 8 warps, kBrPair = one
                            // bootstrap on two CTAs, 0 = tuned or by batch size
+    int ks_kernel;         // key-switch kernel: kKsTiled, j-chunks 1 .. 32 of the
+                           // direct kernel, 0 = tuned or by batch size
     // Autotuned launch shapes per level-width bucket (0 = not tuned): bucket b
     // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
     int8_t tune_br[8];     // bootstraps per blind-rotation CTA
-    int8_t tune_ks[8];     // key-switch j-chunks
+    int8_t tune_ks[8];     // key-switch kernel: kKsTiled, or j-chunks 1 .. 32
 };
 
 constexpr long kTuneEdge[8] = {152, 304, 608, 1216, 2432, 4864, 9728, 1L << 40};

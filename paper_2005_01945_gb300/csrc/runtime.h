@@ -64,9 +64,9 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
 cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
                              const int32_t *idx_out, long rows_out, long count, int n,
                              int num_sms, uint32_t *status, cudaStream_t stream,
-                             const int8_t *tuned = nullptr);
+                             const DevKeys *choice = nullptr);
 
-int keyswitch_kernels(long count, int num_sms, const int8_t *tuned = nullptr);
+int keyswitch_kernels(long count, int num_sms, const DevKeys *choice = nullptr);
 void keyswitch_force_chunks(int chunks);
 
 void release_circuits(tfhe_ctx *ctx);

@@ -332,7 +332,7 @@ static void srv_loop(Server *Sp)
         if (e == cudaSuccess)
             e = launch_keyswitch(ctx->keys.ksk, S.big, S.pool, I.d_idx + 3 * icap, S.pool_rows,
                                  count, ctx->prm.n, ctx->num_sms, ctx->status, S.st,
-                                 ctx->keys.tune_ks);
+                                 &ctx->keys);
         o = 0;
         for (SrvReq *r : finishing) {
             const long no = (long)r->nl->out.size();
@@ -351,7 +351,7 @@ static void srv_loop(Server *Sp)
         I.gates = count;
         {
             std::lock_guard<std::mutex> lock(S.mu);
-            ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms, ctx->keys.tune_ks) +
+            ctx->launches += 1 + keyswitch_kernels(count, ctx->num_sms, &ctx->keys) +
                              (long)finishing.size();
             S.stats.gates += count;
             S.stats.iterations++;

@@ -1,8 +1,9 @@
 // tune.cu -- autotuner for the launch shapes of the two bootstrapping
 // kernels: the blind-rotation CTA shape (1, 2 or 4 bootstraps per CTA in
 // lockstep, one bootstrap spread over 8 warps, or one bootstrap on a
-// cluster of two CTAs) and the
-// key switch's j-split (1 .. 32 chunks), chosen per level-width bucket by
+// cluster of two CTAs) and the key-switch kernel (the tiled kernel with
+// shared-memory key stages, or the direct kernel with its j-split of
+// 1 .. 32 chunks), chosen per level-width bucket by
 // timing the candidates on synthetic ciphertexts with the context's keys.
 // Results can be cached in a small text file keyed by device name and SM
 // count.  Launch shapes never change results (the arithmetic is exact and
@@ -147,9 +148,9 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
                 }
             }
             best = 1e30f;
-            for (int c : {1, 2, 4, 8, 16, 32}) {
-                if ((W + 15) / 16 * c > 64L * ctx->num_sms)   // far more CTAs than useful
-                    continue;
+            for (int c : {kKsTiled, 1, 2, 4, 8, 16, 32}) {
+                if (c != kKsTiled && (W + 15) / 16 * c > 64L * ctx->num_sms)
+                    continue;   // far more CTAs than useful
                 keyswitch_force_chunks(c);
                 float tot = 0;
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {

@@ -118,7 +118,8 @@ def test_blind_rotate_extract_stage(gpu, orc):
 
 @pytest.mark.parametrize("count", [3, 5000])
 def test_keyswitch_stage(gpu, orc, count):
-    """Small batches take the split-j atomic path, large ones the direct one."""
+    """The default key switch (tiled kernel): a small batch splits j over
+    many CTAs (reductions into the output), a large one stores directly."""
     torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
     rng = np.random.default_rng(count)
     big = rng.integers(0, M32, size=(count, 1056), dtype=np.uint64).astype(np.uint32)
@@ -129,6 +130,55 @@ def test_keyswitch_stage(gpu, orc, count):
     got = _u32(out)[sample]
     assert np.array_equal(got[:, :p.n + 1], want)
     assert not got[:, p.n + 1:].any()
+
+
+@pytest.mark.parametrize("kernel,count", [(64, 1), (64, 63), (64, 65), (64, 700), (64, 5000),
+                                          (1, 40), (4, 40), (32, 300)])
+def test_keyswitch_kernels_bit_exact(gpu, orc, kernel, count):
+    """Each key-switch kernel on uniform LWE_N samples: the tiled kernel
+    (64 gates per CTA, key rows staged in shared memory) on one gate, a
+    ragged tile, two tiles, a j-split over 11 tiles (reductions into the
+    output) and 79 tiles (direct stores, no split); the direct kernel with
+    1, 4 and 32 j-chunks.  Sampled rows (and the first and last) are
+    bit-exact against the oracle; padding words stay zero."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    rng = np.random.default_rng(1000 + count + kernel)
+    big = rng.integers(0, M32, size=(count, 1056), dtype=np.uint64).astype(np.uint32)
+    out = torch.full((count, 512), -1, dtype=torch.int32, device="cuda")
+    gpu["ctx"].set_option(api.OPT_KS_KERNEL, kernel)
+    try:
+        gpu["ctx"].keyswitch(api.to_device(big), out)
+    finally:
+        gpu["ctx"].set_option(api.OPT_KS_KERNEL, 0)
+    if count <= 70:
+        sample = np.arange(count)
+    else:
+        sample = np.unique(np.concatenate([[0, count - 1],
+                                           rng.choice(count, 40, replace=False)]))
+    want = orc.keyswitch(P, gpu["oksk"], np.ascontiguousarray(big[sample, :p.N + 1]))
+    got = _u32(out)[sample]
+    assert np.array_equal(got[:, :p.n + 1], want)
+    assert not got[:, p.n + 1:].any()
+    assert gpu["ctx"].status() == 0
+
+
+def test_keyswitch_kernels_agree_on_gates(gpu, orc):
+    """Whole gates (blind rotation + key switch) with the tiled key switch
+    and with the direct one give identical ciphertexts."""
+    torch, api = gpu["torch"], gpu["api"]
+    count = 300
+    bits, cts, dev = _fresh(gpu, orc, count, 55, "ksk2")
+    ops = (np.arange(count) % 6).astype(np.uint8)
+    outs = []
+    for kernel in (api.KS_TILED, 8):
+        out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+        gpu["ctx"].set_option(api.OPT_KS_KERNEL, kernel)
+        try:
+            gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+        finally:
+            gpu["ctx"].set_option(api.OPT_KS_KERNEL, 0)
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_trivial_keys_exact_rotation_large_batch(orc):
@@ -211,7 +261,7 @@ def test_autotune_keeps_results(gpu, orc):
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], before)
     choices = gpu["ctx"].autotune()
     assert set(choices["br_group"].values()) <= {1, 2, 4, 8, 16}
-    assert set(choices["ks_chunks"].values()) <= {1, 2, 4, 8, 16, 32}
+    assert set(choices["ks_chunks"].values()) <= {1, 2, 4, 8, 16, 32, api.KS_TILED}
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], after)
     assert torch.equal(before, after)
     want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
