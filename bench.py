@@ -46,6 +46,9 @@ GATES_PER_ADD = 5 * WIDTH - 6
 # extractions at 8 ops, 2 x 1024 CRT lifts + accumulates at 12 ops.
 OPS_PER_CMUX = 12 * 5120 * 7 + 12 * 1024 * 3 + 4 * 1024 * 12 + 4 * 1024 * 8 + 2 * 1024 * 12
 INT32_LANES_PER_SM = 128
+# Key-switching key as the algorithm reads it: N x t x (base - 1) LWE rows of
+# n + 1 words (the padding to 512 words is layout, not algorithm).
+KSK_BYTES = 1024 * 8 * 3 * 501 * 4
 
 
 def max_over_ranks(value, dist, device=None):
@@ -76,6 +79,10 @@ def parse():
     ap.add_argument("--br-only", type=int, default=0, help="profile mode: blind rotation alone")
     ap.add_argument("--br-group", type=int, default=0, help="blind-rotation CTA shape: 1, 2, 4 bootstraps per CTA, 8 = one "
                          "bootstrap on 8 warps, 16 = one bootstrap on two CTAs (0: automatic)")
+    ap.add_argument("--ks-only", type=int, default=0,
+                    help="profile mode: key switch alone on this many uniform LWE_N samples")
+    ap.add_argument("--ks-kernel", type=int, default=0,
+                    help="key-switch kernel: 64 tiled, 1..32 direct with that j-split (0: default)")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson requests at 3 rates (config 4)")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -270,6 +277,39 @@ def run_br_only(count, group=0):
         ks.append(e1.elapsed_time(e2))
     print(json.dumps({"br_only": count, "group": group, "br_ms": br, "ks_ms": ks,
                       "bootstraps_per_s": count / (min(br) / 1e3)}), flush=True)
+    ctx.close()
+
+
+def run_ks_only(count, kernel=0):
+    """Key switch alone on `count` uniform LWE_N samples (profiling): CUDA
+    event times of 5 launches after a warm-up, and the rate of key bytes."""
+    import torch
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    kd = synth.key_draws(p, synth.MASTER_SEED)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    ctx.set_option(api.OPT_KS_KERNEL, kernel)
+    big = d(synth._gen(11, "ksonly").integers(0, 1 << 32, size=(count, api.BIG_STRIDE),
+                                              dtype=np.uint64).astype(np.uint32).view(np.int32))
+    out = torch.empty((count, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.keyswitch(big, out)
+    ms = []
+    for _ in range(5):
+        e0.record()
+        ctx.keyswitch(big, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    alg = KSK_BYTES + count * (p.N + 1 + p.n + 1) * 4
+    print(json.dumps({"ks_only": count, "kernel": kernel or "default", "ks_ms": ms,
+                      "algorithmic_bytes": alg, "gb_per_s": alg / (min(ms) / 1e3) / 1e9,
+                      "status": ctx.status()}), flush=True)
     ctx.close()
 
 
@@ -575,6 +615,9 @@ def main():
     if args.br_only:
         run_br_only(args.br_only, args.br_group)
         return
+    if args.ks_only:
+        run_ks_only(args.ks_only, args.ks_kernel)
+        return
     if args.serve:
         run_serve(args)
         return
@@ -702,6 +745,19 @@ def main():
                 "launches": br_launch, "avg_launch_ms": br_ms / max(br_launch, 1),
                 "share_of_step": br_ms / max(sum(step_ms), 1e-9),
                 "keyswitch_share_of_step": ks_ms / max(sum(step_ms), 1e-9)}
+    # key switch (one call per level: the tiled kernel and its output
+    # initialisation), against HBM: algorithmic bytes = the key once + the
+    # level's LWE_N inputs and LWE_n outputs
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ks_calls = max(br_launch, 1)
+    ks_bytes = KSK_BYTES + br_boot / ks_calls * (p.N + 1 + p.n + 1) * 4
+    ks_gbs = ks_bytes / (ks_ms / ks_calls / 1e3) / 1e9 if ks_ms > 0 else 0.0
+    keyswitch = {"kernel": "k_keyswitch_tiled", "bound": "smem", "achieved_hbm": ks_gbs,
+                 "peak_hbm": hbm, "unit": "GB/s", "frac_hbm": ks_gbs / hbm,
+                 "algorithmic_bytes_per_call": ks_bytes, "calls": ks_calls,
+                 "avg_call_ms": ks_ms / ks_calls,
+                 "note": "reads the key once per call from DRAM; bound by shared-memory "
+                         "bandwidth (selected key rows delivered per gate), not HBM"}
 
     # ---- 32-bit multiplication latency: level-batched vs one launch pair per gate
     latency = None
@@ -760,6 +816,7 @@ def main():
                            "autotuned": tuned,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "keyswitch": keyswitch,
                 "cpu_baseline": cpu, "mul32_latency": latency, "verified": verified}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -170,7 +170,6 @@ struct KtSmem {
     uint4 raw[kKtStages][kKtRows][kKtVecs];          // 48 KB ring: KSK[j][q][d] halves
     uint4 combo[kKtPairs][kKtCombos][kKtVecs];       // 36 KB: KSK[j][2p][d1] + KSK[j][2p+1][d2]
     uint4 zero[kKtVecs];                             // 1 KB of zeros (digit pair 00)
-    uint32_t off[kKtStages][kKtPairs][16];           // row of digit pair 4 d1 + d2
     uint16_t w[kKtWin][kKtWStride];                  // rounded a'_j [j][gate] (18 KB)
     unsigned long long full[kKtStages];              // mbarriers: stage landed
     int abort;
@@ -178,6 +177,37 @@ struct KtSmem {
 static_assert(sizeof(uint4) * (kKtStages * kKtRows + kKtPairs * kKtCombos) * kKtVecs >=
                   sizeof(uint32_t) * kKtTile * kKtCols,
               "partial sums must fit in the raw ring and the combination rows");
+
+// Row (in uint4 from KtSmem::raw) that digit pair value 4 d1 + d2 of pair p
+// selects in ring slot `slot`: zeros, KSK[2p][d1] (d2 = 0), KSK[2p+1][d2]
+// (d1 = 0) or the built sum.  A fixed table in the constant bank: the
+// warp-uniform lookups go through the constant cache, not shared memory.
+struct KtOffsets {
+    uint32_t v[kKtStages][kKtPairs][16];
+};
+
+constexpr KtOffsets make_kt_offsets()
+{
+    KtOffsets T{};
+    for (int slot = 0; slot < kKtStages; ++slot)
+        for (int p = 0; p < kKtPairs; ++p)
+            for (int idx = 0; idx < 16; ++idx) {
+                const int d1 = idx >> 2, d2 = idx & 3;
+                int r = 0;
+                if (idx == 0)
+                    r = kKtStages * kKtRows + kKtPairs * kKtCombos;
+                else if (d2 == 0)
+                    r = slot * kKtRows + (2 * p) * kKsDigits + d1 - 1;
+                else if (d1 == 0)
+                    r = slot * kKtRows + (2 * p + 1) * kKsDigits + d2 - 1;
+                else
+                    r = kKtStages * kKtRows + p * kKtCombos + (d1 - 1) * kKsDigits + d2 - 1;
+                T.v[slot][p][idx] = (uint32_t)(r * kKtVecs);
+            }
+    return T;
+}
+
+__constant__ KtOffsets c_kt_off = make_kt_offsets();
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -289,20 +319,6 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
     }
     if (tid < kKtVecs)
         S.zero[tid] = make_uint4(0u, 0u, 0u, 0u);
-    if (tid < kKtStages * kKtPairs * 16) {
-        const int slot = tid / (kKtPairs * 16), p = (tid / 16) % kKtPairs, idx = tid % 16;
-        const int d1 = idx >> 2, d2 = idx & 3;
-        int r;   // row index in uint4-rows of kKtVecs, counted from S.raw
-        if (idx == 0)
-            r = kKtStages * kKtRows + kKtPairs * kKtCombos;                  // zero row
-        else if (d2 == 0)
-            r = slot * kKtRows + (2 * p) * kKsDigits + d1 - 1;                 // KSK[2p][d1]
-        else if (d1 == 0)
-            r = slot * kKtRows + (2 * p + 1) * kKsDigits + d2 - 1;             // KSK[2p+1][d2]
-        else
-            r = kKtStages * kKtRows + p * kKtCombos + (d1 - 1) * kKsDigits + d2 - 1;
-        S.off[slot][p][idx] = (uint32_t)(r * kKtVecs);
-    }
     __syncthreads();
 
     uint32_t it = 0;       // stages consumed so far (slot = it % kKtStages)
@@ -361,7 +377,7 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
             if (!S.abort) {
                 const uint4 wq = *reinterpret_cast<const uint4 *>(&S.w[kw][warp * kKtGpw]);
                 const uint32_t wv[4] = {wq.x, wq.y, wq.z, wq.w};
-                const uint32_t *off = &S.off[slot][0][0];
+                const uint32_t *off = &c_kt_off.v[slot][0][0];
 #pragma unroll 1
                 for (int p = 0; p < kKtPairs; ++p)
 #pragma unroll
