@@ -369,7 +369,8 @@ def run_variants(args):
     ma, mb = synth.int_pairs(64, 32, seed, "var_mul")
     MA, MB = enc(ma, 32, "vma"), enc(mb, 32, "vmb")
     MR = torch.empty_like(MA)
-    for name, kind in (("sequential", api.MUL), ("tree", api.MUL_TREE)):
+    for name, kind in (("sequential", api.MUL), ("tree", api.MUL_TREE),
+                       ("tree_maj", api.MUL_TREE_MAJ)):
         job = [dict(kind=kind, width=32, batch=64, in0=MA, in1=MB, out=MR)]
         ms = timed(lambda: ctx.run_jobs(job), 2)
         g, depth = api.circuit_info(kind, 32)
@@ -759,8 +760,10 @@ def main():
                  "note": "reads the key once per call from DRAM; bound by shared-memory "
                          "bandwidth (selected key rows delivered per gate), not HBM"}
 
-    # ---- 32-bit multiplication latency: level-batched vs one launch pair per gate
-    latency = None
+    # ---- 32-bit multiplication latency: level-batched vs one launch pair per
+    # gate, for the sequential shift-and-add multiplier and for the
+    # tree-accumulated one with majority-carry adders
+    latency = latency_tree = None
     if not args.no_latency and rank == 0:
         ma, mb = synth.int_pairs(1, 32, seed + 2, "lat")
         da = api.encrypt_bits(p, s_dev, d(synth.ct_draws(p, (1, 32), seed + 2, "la").mask),
@@ -770,33 +773,45 @@ def main():
                               d(synth.ct_draws(p, (1, 32), seed + 2, "lb").noise),
                               d(synth.to_bits(mb, 32)))
         out = torch.empty((1, 32, api.LWE_STRIDE), dtype=torch.int32, device=dev)
+        want = (int(ma[0]) * int(mb[0])) % (1 << 32)
 
-        def timed(nsamp):
-            res = []
-            ctx.mul_n(32, da, db, out)
-            torch.cuda.synchronize()
-            for _ in range(nsamp):
-                e0.record()
-                ctx.mul_n(32, da, db, out)
-                e1.record()
+        def measure(kind, per_gate_samples):
+            job = [dict(kind=kind, width=32, batch=1, in0=da, in1=db, out=out)]
+
+            def timed(nsamp):
+                res = []
+                ctx.run_jobs(job)
                 torch.cuda.synchronize()
-                res.append(e0.elapsed_time(e1))
-            return res
+                for _ in range(nsamp):
+                    e0.record()
+                    ctx.run_jobs(job)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    res.append(e0.elapsed_time(e1))
+                return res
 
-        batched = timed(args.latency_samples)
-        ok_b = bool(synth.from_bits(api.decrypt_bits(p, s_dev, out).cpu().numpy())[0]
-                    == (int(ma[0]) * int(mb[0])) % (1 << 32))
-        ctx.set_option(api.OPT_PER_GATE, 1)
-        per_gate = timed(args.per_gate_samples)
-        ctx.set_option(api.OPT_PER_GATE, 0)
-        ok_p = bool(synth.from_bits(api.decrypt_bits(p, s_dev, out).cpu().numpy())[0]
-                    == (int(ma[0]) * int(mb[0])) % (1 << 32))
-        pct = lambda xs, q: float(np.percentile(np.array(xs), q))  # noqa: E731
-        latency = {"request": "one 32x32->32 multiplication (2,824 gates, 120 levels) alone",
-                   "batched_p50_ms": pct(batched, 50), "batched_p99_ms": pct(batched, 99),
-                   "batched_samples": len(batched),
-                   "per_gate_p50_ms": pct(per_gate, 50), "per_gate_p99_ms": pct(per_gate, 99),
-                   "per_gate_samples": len(per_gate), "verified": ok_b and ok_p}
+            ok = lambda: bool(synth.from_bits(api.decrypt_bits(p, s_dev, out).cpu().numpy())[0]  # noqa: E731
+                              == want)
+            batched = timed(args.latency_samples)
+            ok_b = ok()
+            ctx.set_option(api.OPT_PER_GATE, 1)
+            per_gate = timed(per_gate_samples)
+            ctx.set_option(api.OPT_PER_GATE, 0)
+            ok_p = ok()
+            gates, depth = api.circuit_info(kind, 32)
+            pct = lambda xs, q: float(np.percentile(np.array(xs), q))  # noqa: E731
+            return {"gates": gates, "levels": depth,
+                    "batched_p50_ms": pct(batched, 50), "batched_p99_ms": pct(batched, 99),
+                    "batched_samples": len(batched),
+                    "per_gate_p50_ms": pct(per_gate, 50), "per_gate_p99_ms": pct(per_gate, 99),
+                    "per_gate_samples": len(per_gate), "verified": ok_b and ok_p}
+
+        latency = measure(api.MUL, args.per_gate_samples)
+        latency["request"] = ("one 32x32->32 sequential shift-and-add multiplication "
+                              "(2,824 gates, 120 levels) alone")
+        latency_tree = measure(api.MUL_TREE_MAJ, 1)
+        latency_tree["request"] = ("one 32x32->32 multiplication, partial products summed by a "
+                                   "tree of majority-carry adders (1,954 gates, 40 levels) alone")
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
@@ -817,7 +832,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "keyswitch": keyswitch,
-                "cpu_baseline": cpu, "mul32_latency": latency, "verified": verified}
+                "cpu_baseline": cpu, "mul32_latency": latency,
+                "mul32_tree_maj_latency": latency_tree, "verified": verified}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -195,11 +195,14 @@ typedef enum {
     TFHE_CIRCUIT_MUL_FULL = 7, /* full product, w x w -> 2w bits, 2 <= w <= 64:  */
                                /*   AND partial products at their weights summed  */
                                /*   by the tree of section V-B-2                  */
-    TFHE_CIRCUIT_MUL_KARATSUBA = 8 /* full product by Karatsuba (Algorithm        */
+    TFHE_CIRCUIT_MUL_KARATSUBA = 8, /* full product by Karatsuba (Algorithm       */
                                /*   "karatsuba", vector form of section V-B),     */
                                /*   split at ceil(w/2), Z2 - (Z0 + Z1) by a       */
                                /*   two's-complement subtractor, the full product */
                                /*   above below 8 bits; 2w bits, 2 <= w <= 64     */
+    TFHE_CIRCUIT_MUL_TREE_MAJ = 9 /* MUL_TREE whose adders carry with majority    */
+                               /*   gates (one MAJ per carry): fewer gates and    */
+                               /*   about half the depth, for latency             */
 } tfhe_circuit;
 
 typedef struct {

@@ -80,6 +80,7 @@ def lib():
             "orc_add_maj": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_add_nw": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_tree": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_mul_tree_maj": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_full": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_karatsuba": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_blind_rotate_many": (None, [P, vp, i64, vp, u32, vp, i32]),
@@ -273,6 +274,11 @@ def add_nw(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
 def mul_tree(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
     """Multiplication with tree-based accumulation -> (R, gates)."""
     return _circuit("orc_mul_tree", P, bk, ksk, w, A, B, nthreads)
+
+
+def mul_tree_maj(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Tree-accumulated multiplication with majority-carry adders -> (R, gates)."""
+    return _circuit("orc_mul_tree_maj", P, bk, ksk, w, A, B, nthreads)
 
 
 def _full(name, P, bk, ksk, w, A, B, nthreads):

@@ -702,8 +702,10 @@ static void ev_add_nw(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *
 /* Truncated multiplication with tree-based accumulation (section V-B-2):
  * partial product i is A AND b_i shifted left by i (its low i bits the
  * constant 0); the w partial products are added pairwise, (0,1), (2,3),
- * ..., an odd last one moving up unchanged, until one is left. */
-static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
+ * ..., an odd last one moving up unchanged, until one is left.  The adders
+ * carry by Eq. "addcarry" (maj = 0) or by single majority gates (maj = 1). */
+static void ev_mul_tree_with(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
+                             uint32_t *R, int maj)
 {
     const int64_t W = E->P->n + 1;
     orc_arena A = {NULL, 0, 0, W};
@@ -721,7 +723,7 @@ static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t
     while (cnt > 1) {
         int32_t k = 0;
         for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
-            ev_add_cells(E, &A, w, terms + i * w, terms + (i + 1) * w, 0, next + k * w);
+            ev_add_cells(E, &A, w, terms + i * w, terms + (i + 1) * w, maj, next + k * w);
         if (cnt & 1) {
             memcpy(next + k * w, terms + (cnt - 1) * w, sizeof(*terms) * w);
             k++;
@@ -732,6 +734,17 @@ static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t
     copy_out(w, W, terms, R);
     free(terms); free(next);
     arena_free(&A);
+}
+
+static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
+{
+    ev_mul_tree_with(E, w, Av, Bv, R, 0);
+}
+
+static void ev_mul_tree_maj(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
+                            uint32_t *R)
+{
+    ev_mul_tree_with(E, w, Av, Bv, R, 1);
 }
 
 /* Full product Z = X Y of n-bit X, Y as 2n bits (section III-B-1, "Naive
@@ -994,6 +1007,13 @@ int64_t orc_mul_tree(const orc_params *P, const uint32_t *bk, const uint32_t *ks
                      int32_t nthreads)
 {
     return run_batched(ev_mul_tree, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_mul_tree_maj(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                     int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                     int32_t nthreads)
+{
+    return run_batched(ev_mul_tree_maj, P, bk, ksk, w, batch, A, B, R, nthreads);
 }
 
 int64_t orc_matvec(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,

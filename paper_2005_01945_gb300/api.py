@@ -98,7 +98,7 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
 }
 
-GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA = range(9)
+GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA, MUL_TREE_MAJ = range(10)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH, \
     OPT_KS_KERNEL = range(7)
 KS_TILED = 64   # OPT_KS_KERNEL value of the tiled key-switch kernel

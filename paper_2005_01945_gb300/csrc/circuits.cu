@@ -150,9 +150,10 @@ static std::vector<int> build_add_numberwise(Netlist &nl, const std::vector<int>
 // Truncated multiplication with tree-based accumulation (section V-B-2):
 // partial products A AND b_i shifted by i (low i bits constant 0) are
 // summed pairwise, (0,1), (2,3), ..., an odd last term moving up, with
-// ripple-carry adders that skip constant-zero bits.
+// ripple-carry adders that skip constant-zero bits (carries of Eq.
+// "addcarry", or single majority gates when maj).
 static std::vector<int> build_mul_tree(Netlist &nl, const std::vector<int> &x,
-                                       const std::vector<int> &y)
+                                       const std::vector<int> &y, bool maj)
 {
     const int w = (int)x.size();
     std::vector<std::vector<int>> terms;
@@ -165,7 +166,7 @@ static std::vector<int> build_mul_tree(Netlist &nl, const std::vector<int> &x,
     while (terms.size() > 1) {
         std::vector<std::vector<int>> next;
         for (size_t i = 0; i + 1 < terms.size(); i += 2)
-            next.push_back(build_add_const(nl, terms[i], terms[i + 1], false));
+            next.push_back(build_add_const(nl, terms[i], terms[i + 1], maj));
         if (terms.size() & 1)
             next.push_back(terms.back());
         terms.swap(next);
@@ -310,6 +311,7 @@ bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
     case TFHE_CIRCUIT_ADD_MAJ:
     case TFHE_CIRCUIT_ADD_NW:
     case TFHE_CIRCUIT_MUL_TREE:
+    case TFHE_CIRCUIT_MUL_TREE_MAJ:
         if (w < 1 || w > 64)
             return false;
         nl.n_in = 2 * w;
@@ -317,7 +319,8 @@ bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
                      ? build_add_const(nl, range_wires(0, w), range_wires(w, w), true)
                  : kind == TFHE_CIRCUIT_ADD_NW
                      ? build_add_numberwise(nl, range_wires(0, w), range_wires(w, w))
-                     : build_mul_tree(nl, range_wires(0, w), range_wires(w, w));
+                     : build_mul_tree(nl, range_wires(0, w), range_wires(w, w),
+                                      kind == TFHE_CIRCUIT_MUL_TREE_MAJ);
         for (int o : nl.out)
             if (o < 0)
                 return false;
@@ -531,10 +534,11 @@ struct Schedule {
 // Deadline-driven list scheduling (policy TFHE_SCHED_BALANCED): gate g of a
 // netlist has ASAP level asap(g) and, for the schedule depth D, ALAP level
 // alap(g) = D + 1 - height(g), height = longest path to an output.  Level L
-// takes every ready gate whose deadline is L, then fills up to `target`
-// gates with the ready gates of the earliest deadlines.  By induction every
-// gate is ready by its deadline, so the depth stays D; widths exceed the
-// target only where the deadlines force it.  The ciphertexts do not depend
+// takes every ready gate whose deadline is L, then fills up to the next
+// multiple of `target` (one GPU wave; at least one) with the ready gates of
+// the earliest deadlines, so that no launch ends in a part-empty wave while
+// work is ready.  By induction every gate is ready by its deadline, so the
+// depth stays D; widths exceed one wave only where the deadlines force it.  The ciphertexts do not depend
 // on the schedule (each gate is a deterministic function of its inputs).
 static void balanced_levels(const std::vector<const Netlist *> &nets, const std::vector<long> &batch,
                             int D, long target, std::vector<std::vector<int32_t>> &level)
@@ -592,11 +596,17 @@ static void balanced_levels(const std::vector<const Netlist *> &nets, const std:
     std::vector<long> chosen, fresh;
     for (int L = 1; done < total; ++L) {
         chosen.clear();
-        for (int a = 1; a <= D; ++a) {      // deadline L (and, defensively, earlier) first
-            if (a > L && (long)chosen.size() >= target)
-                break;
+        for (int a = 1; a <= L && a <= D; ++a) {   // deadline L (and, defensively, earlier)
             std::vector<long> &B = bucket[a];
-            while (head[a] < B.size() && (a <= L || (long)chosen.size() < target))
+            while (head[a] < B.size())
+                chosen.push_back(B[head[a]++]);
+        }
+        // fill the last wave the forced gates leave open (at least one
+        // wave) with the ready gates of the earliest deadlines
+        const long cap = std::max(target, ((long)chosen.size() + target - 1) / target * target);
+        for (int a = L + 1; a <= D && (long)chosen.size() < cap; ++a) {
+            std::vector<long> &B = bucket[a];
+            while (head[a] < B.size() && (long)chosen.size() < cap)
                 chosen.push_back(B[head[a]++]);
         }
         fresh.clear();

@@ -217,10 +217,12 @@ def test_config3_matvec16(full):
 
 
 @pytest.mark.parametrize("kind_name,w", [("ADD_MAJ", 32), ("ADD_NW", 8), ("MUL_TREE", 8),
-                                         ("ADD_MAJ", 1), ("MUL_TREE", 3)])
+                                         ("ADD_MAJ", 1), ("MUL_TREE", 3), ("MUL_TREE_MAJ", 8),
+                                         ("MUL_TREE_MAJ", 5)])
 def test_next_circuits_bit_exact(small, kind_name, w):
     """Majority-carry adder (3-input MAJ gates), the paper's number-wise adder
-    and tree-accumulated multiplication, bit-exact against the oracle."""
+    and tree-accumulated multiplication (ripple or majority carries),
+    bit-exact against the oracle."""
     E = small
     api = E.api
     kind = getattr(api, kind_name)
@@ -229,7 +231,8 @@ def test_next_circuits_bit_exact(small, kind_name, w):
     db, ob = E.enc_ints(b, w, 12, f"nb{kind_name}{w}")
     R = E.out((2, w))
     E.ctx.run_jobs([dict(kind=kind, width=w, batch=2, in0=da, in1=db, out=R)])
-    fn = {"ADD_MAJ": E.orc.add_maj, "ADD_NW": E.orc.add_nw, "MUL_TREE": E.orc.mul_tree}[kind_name]
+    fn = {"ADD_MAJ": E.orc.add_maj, "ADD_NW": E.orc.add_nw, "MUL_TREE": E.orc.mul_tree,
+          "MUL_TREE_MAJ": E.orc.mul_tree_maj}[kind_name]
     want, g = fn(E.P, E.obk, E.oksk, w, oa, ob)
     got = E.host(R)
     assert np.array_equal(got, want)

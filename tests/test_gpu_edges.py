@@ -2,7 +2,8 @@
 inputs, parameter sets outside the supported range, trivial (zero-mask)
 ciphertexts for which every CMux is skipped, the largest LWE dimension
 (n = 511) bit-exact against the oracle, and a 100,000-gate batch checked
-by decryption on every output and by the oracle on a sample."""
+by decryption on every output and by the oracle on a sample, and a key
+switch over more tiles than one launch grid holds."""
 import numpy as np
 import pytest
 
@@ -154,4 +155,32 @@ def test_hundred_thousand_gates(env):
     sample = synth._gen(41, "big-sample").choice(count, 8, replace=False)
     want = orc.gates(env.P, env.obk, env.oksk, ops[sample], cts[0][sample], cts[1][sample])
     assert np.array_equal(got[sample, :p.n + 1], want)
+    assert env.ctx.status() == 0
+
+
+def test_keyswitch_beyond_one_grid_of_tiles(env):
+    """4,194,310 LWE_N samples: 65,537 tiles of 64 gates, more than the
+    65,535 that one launch grid holds, so the tiled key switch's CTAs loop
+    over a second tile.  Rows around both grid boundaries (and the last,
+    ragged tile) are bit-exact against the oracle."""
+    torch, api, orc, p = env.torch, env.api, env.orc, env.p
+    count = 65535 * 64 + 70
+    gen = torch.Generator(device="cuda").manual_seed(17)
+    big = torch.randint(-2**31, 2**31 - 1, (count, api.BIG_STRIDE), dtype=torch.int32,
+                        device="cuda", generator=gen)
+    out = torch.empty((count, 512), dtype=torch.int32, device="cuda")
+    env.ctx.set_option(api.OPT_KS_KERNEL, api.KS_TILED)
+    try:
+        env.ctx.keyswitch(big, out)
+    finally:
+        env.ctx.set_option(api.OPT_KS_KERNEL, 0)
+    edge = 65535 * 64
+    sample = np.array([0, 63, 64, edge - 1, edge, edge + 63, edge + 64, count - 1])
+    idx = torch.from_numpy(sample).cuda()
+    rows = big.index_select(0, idx).cpu().numpy().view(np.uint32)
+    got = out.index_select(0, idx).cpu().numpy().view(np.uint32)
+    del big, out
+    want = orc.keyswitch(env.P, env.oksk, np.ascontiguousarray(rows[:, :p.N + 1]))
+    assert np.array_equal(got[:, :p.n + 1], want)
+    assert not got[:, p.n + 1:].any()
     assert env.ctx.status() == 0

@@ -144,17 +144,18 @@ def test_balanced_schedule_invariants():
     assert (wb[:-1] == 608).all() and wb[-1] == 39424 - 61 * 608
 
 
-@pytest.mark.parametrize("name", ["add_maj", "add_nw", "mul_tree"])
+@pytest.mark.parametrize("name", ["add_maj", "add_nw", "mul_tree", "mul_tree_maj"])
 @pytest.mark.parametrize("w", [1, 2, 3, 4])
 def test_new_circuits_exhaustive(orc, toy, name, w):
     """Majority-carry adder, the paper's number-wise adder GPU_n and
-    tree-accumulated multiplication: every input pair at toy parameters."""
+    tree-accumulated multiplication (ripple or majority carries): every
+    input pair at toy parameters."""
     p, P, kd, bk, ksk = toy
     a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
     a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
     R, g = getattr(orc, name)(P, bk, ksk, w, _enc_ints(orc, p, P, kd, a, w, f"{name}a{w}"),
                               _enc_ints(orc, p, P, kd, b, w, f"{name}b{w}"))
-    want = (a * b if name == "mul_tree" else a + b) % (1 << w)
+    want = (a * b if name.startswith("mul") else a + b) % (1 << w)
     assert np.array_equal(_dec_ints(orc, P, kd, R), want)
 
 
@@ -170,7 +171,8 @@ def test_new_circuits_wide_and_counts(orc, toy, w):
     A, B = _enc_ints(orc, p, P, kd, a, w, "nca"), _enc_ints(orc, p, P, kd, b, w, "ncb")
     for name, kind, want in (("add_maj", api.ADD_MAJ, (a + b) % (1 << w)),
                              ("add_nw", api.ADD_NW, (a + b) % (1 << w)),
-                             ("mul_tree", api.MUL_TREE, (a * b) % (1 << w))):
+                             ("mul_tree", api.MUL_TREE, (a * b) % (1 << w)),
+                             ("mul_tree_maj", api.MUL_TREE_MAJ, (a * b) % (1 << w))):
         R, g = getattr(orc, name)(P, bk, ksk, w, A, B)
         assert np.array_equal(_dec_ints(orc, P, kd, R), want), name
         assert g == 3 * api.circuit_info(kind, w)[0], name
