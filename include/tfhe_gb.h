@@ -252,10 +252,16 @@ typedef enum {
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
     TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave,   */
                              /*    4 bootstraps per SM)                             */
-    TFHE_OPT_KS_KERNEL = 6   /* key-switch kernel: 64 = tiled (64 gates per CTA, key */
+    TFHE_OPT_KS_KERNEL = 6,  /* key-switch kernel: 64 = tiled (64 gates per CTA, key */
                              /*    rows staged in shared memory by bulk copies),    */
                              /*    1, 2, 4, .. 32 = direct kernel with that j-split, */
                              /*    or 0 (default): autotuned, else by batch size    */
+    TFHE_OPT_TEST_KS_STALL = 7 /* test hook for the timeout path, 0 (default) off:  */
+                             /*    1 makes every stage of the tiled key switch wait */
+                             /*    for 16 bytes that never arrive, so each bounded  */
+                             /*    wait runs out after a short budget; the call     */
+                             /*    then sets status bit 2 (timeout), its outputs    */
+                             /*    are undefined, and the context stays usable     */
 } tfhe_option;
 
 int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);

@@ -100,7 +100,7 @@ EXPORTS = {
 
 GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA, MUL_TREE_MAJ = range(10)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH, \
-    OPT_KS_KERNEL = range(7)
+    OPT_KS_KERNEL, OPT_TEST_KS_STALL = range(8)
 KS_TILED = 64   # OPT_KS_KERNEL value of the tiled key-switch kernel
 SCHED_ASAP, SCHED_BALANCED = 0, 1
 

@@ -1062,6 +1062,10 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
             return fail(ctx, TFHE_EINVAL, "TFHE_OPT_LEVEL_WIDTH must be >= 0");
         C.level_width = (long)value;
         return TFHE_OK;
+    case TFHE_OPT_TEST_KS_STALL:
+        ctx->keys.ks_stall = value != 0;
+        invalidate_graphs(ctx);
+        return TFHE_OK;
     case TFHE_OPT_KS_KERNEL:
         if (value != 0 && value != kKsTiled &&
             !(value >= 1 && value <= 32 && (value & (value - 1)) == 0))

@@ -86,6 +86,8 @@ struct DevKeys {
                            // bootstrap on two CTAs, 0 = tuned or by batch size
     int ks_kernel;         // key-switch kernel: kKsTiled, j-chunks 1 .. 32 of the
                            // direct kernel, 0 = tuned or by batch size
+    int ks_stall;          // test hook (TFHE_OPT_TEST_KS_STALL): the tiled key
+                           // switch's copy waits run out
     // Autotuned launch shapes per level-width bucket (0 = not tuned): bucket b
     // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
     int8_t tune_br[8];     // bootstraps per blind-rotation CTA

@@ -41,6 +41,9 @@ struct KsArgs {
     int j_chunk;              // j values per CTA (blockIdx.y selects the chunk)
     int atomic;               // 1: add into pre-initialised rows
     uint32_t *status;
+    long spin;                // tiled kernel: tries of one bounded mbarrier wait
+    uint32_t stall_tx;        // tiled kernel, test hook: extra bytes each stage expects
+                              // (non-zero: no stage completes, every wait runs out)
 };
 
 __device__ __forceinline__ long ks_dest(const KsArgs &A, long g)
@@ -163,7 +166,9 @@ constexpr uint32_t kKtStageBytes = kKtRows * kKtCols * 4;   // 24 KB
 constexpr int kKtWin = 128;                          // j values of rounded a'_j held at once
 constexpr int kKtWStride = kKtTile + 8;              // uint16 per window row (padded)
 constexpr int kKtMaxChunks = 128;
-constexpr long kKtSpin = 1L << 22;                   // bounded mbarrier wait (tries)
+constexpr long kKtSpin = 1L << 20;                   // bounded mbarrier wait: tries of at
+constexpr uint32_t kKtTryNs = 1000;                  // most ~1 us each (about a second)
+constexpr long kKtStallSpin = 1L << 10;              // ... under the stall test hook
 
 // raw, combo and zero are contiguous: row offsets below count uint4 from raw.
 struct KtSmem {
@@ -172,7 +177,8 @@ struct KtSmem {
     uint4 zero[kKtVecs];                             // 1 KB of zeros (digit pair 00)
     uint16_t w[kKtWin][kKtWStride];                  // rounded a'_j [j][gate] (18 KB)
     unsigned long long full[kKtStages];              // mbarriers: stage landed
-    int abort;
+    int abort;                                       // a wait ran out: stop
+    uint32_t abort_it;                               // ... at this stage
 };
 static_assert(sizeof(uint4) * (kKtStages * kKtRows + kKtPairs * kKtCombos) * kKtVecs >=
                   sizeof(uint32_t) * kKtTile * kKtCols,
@@ -228,24 +234,26 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t
 }
 
 // One bounded wait on phase `parity` of an mbarrier: the thread is
-// suspended until the phase completes or a hardware time limit passes.
+// suspended until the phase completes or about kKtTryNs pass.
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok)
-                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "r"(smem_addr(bar)), "r"(parity), "r"(kKtTryNs)
                  : "memory");
     return ok != 0;
 }
 
-// Waits for phase `parity`, giving up after kKtSpin suspended tries (far
-// beyond any copy's latency); returns whether the phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity)
+// Waits for phase `parity`, giving up after `spin` suspended tries
+// (kKtSpin: about a second, far beyond any copy's latency); returns whether
+// the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity,
+                                                  long spin)
 {
-    for (long i = 0; i < kKtSpin; ++i)
+    for (long i = 0; i < spin; ++i)
         if (mbar_try_wait(bar, parity))
             return true;
     return false;
@@ -282,7 +290,7 @@ __device__ __forceinline__ void kt_issue(const KsArgs &A, KtSmem &S, int slot, i
 {
     if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&S.full[slot], kKtStageBytes);
+        mbar_expect_tx(&S.full[slot], kKtStageBytes + A.stall_tx);
     }
     __syncwarp();
     if (lane < kKtRows) {
@@ -315,6 +323,7 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
         for (int s = 0; s < kKtStages; ++s)
             mbar_init(&S.full[s], 1);
         S.abort = 0;
+        S.abort_it = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < kKtVecs)
@@ -354,7 +363,8 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
                 __syncthreads();
             }
             const int slot = it % kKtStages;
-            if (!S.abort && !mbar_wait_bounded(&S.full[slot], (it / kKtStages) & 1u)) {
+            if (!S.abort && !mbar_wait_bounded(&S.full[slot], (it / kKtStages) & 1u, A.spin)) {
+                S.abort_it = it;   // the same value in every thread that gets here
                 S.abort = 1;
                 atomicOr(A.status, kErrTimeout);
             }
@@ -449,11 +459,11 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();   // the ring is free for the next tile's copies
     }
-    // after a timed-out wait: give the copies still in flight a bounded
-    // time to land before the CTA's shared memory is released
+    // after a timed-out wait: give the stages issued but never waited for a
+    // bounded time to land before the CTA's shared memory is released
     if (warp == 0 && lane == 0 && S.abort)
-        for (uint32_t p = it; p < issued; ++p)
-            (void)mbar_wait_bounded(&S.full[p % kKtStages], (p / kKtStages) & 1u);
+        for (uint32_t p = S.abort_it; p < issued; ++p)
+            (void)mbar_wait_bounded(&S.full[p % kKtStages], (p / kKtStages) & 1u, A.spin);
 }
 
 // ---------------------------------------------------------------------
@@ -521,6 +531,9 @@ cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
     A.j_chunk = kN / chunks;
     A.atomic = chunks > 1;
     A.status = status;
+    const bool stall = tiled && choice && choice->ks_stall;
+    A.spin = stall ? kKtStallSpin : kKtSpin;
+    A.stall_tx = stall ? 16u : 0u;
     if (A.atomic) {
         k_ks_init<<<(unsigned)count, 128, 0, stream>>>(A);
         cudaError_t e = cudaGetLastError();

@@ -184,3 +184,32 @@ def test_keyswitch_beyond_one_grid_of_tiles(env):
     assert np.array_equal(got[:, :p.n + 1], want)
     assert not got[:, p.n + 1:].any()
     assert env.ctx.status() == 0
+
+
+def test_keyswitch_wait_timeout_is_reported_and_recoverable(env):
+    """Failure detection without a GPU fault: with the stall test hook every
+    stage of the tiled key switch waits on an mbarrier for 16 bytes that no
+    copy delivers.  Each bounded wait runs out, the kernel records the
+    timeout (status bit 2) and returns; the next call on the same context,
+    hook off, is bit-exact against the oracle."""
+    torch, api, orc, p = env.torch, env.api, env.orc, env.p
+    count = 70
+    rng = np.random.default_rng(23)
+    big = rng.integers(0, 1 << 32, size=(count, api.BIG_STRIDE), dtype=np.uint64)
+    big = big.astype(np.uint32)
+    dbig = api.to_device(big)
+    out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    env.ctx.set_option(api.OPT_KS_KERNEL, api.KS_TILED)
+    try:
+        env.ctx.set_option(api.OPT_TEST_KS_STALL, 1)
+        try:
+            env.ctx.keyswitch(dbig, out)
+        finally:
+            env.ctx.set_option(api.OPT_TEST_KS_STALL, 0)
+        assert env.ctx.status() == 4
+        env.ctx.keyswitch(dbig, out)
+    finally:
+        env.ctx.set_option(api.OPT_KS_KERNEL, 0)
+    want = orc.keyswitch(env.P, env.oksk, np.ascontiguousarray(big[:, :p.N + 1]))
+    assert np.array_equal(_u32(out)[:, :p.n + 1], want)
+    assert env.ctx.status() == 0

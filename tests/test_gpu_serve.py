@@ -123,3 +123,34 @@ def test_small_pool_forces_queueing(env):
     assert stats["completed"] == len(reqs)
     for a, b in zip(roomy, tight):
         assert np.array_equal(a, b)
+
+
+def test_wait_timeout_then_result(env):
+    """A client wait that runs out is reported, not hung: waiting 1 ms on a
+    16-bit multiplication (56 levels, well over 1 ms) raises TFHE_ETIMEOUT;
+    the request keeps running and a second wait returns its result, equal
+    to the oracle's."""
+    torch, api, p, P, kd = env["torch"], env["api"], env["p"], env["P"], env["kd"]
+    orc = __import__("oracle")
+    d = api.to_device
+    s_dev = d(kd.s)
+    bits = [synth.random_bits((16,), 91, f"to{j}") for j in range(2)]
+    cds = [synth.ct_draws(p, b.shape, 91, f"to{j}") for j, b in enumerate(bits)]
+    dev = [api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(b)) for cd, b in zip(cds, bits)]
+    host = [orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, b) for cd, b in zip(cds, bits)]
+    out = torch.zeros((16, 512), dtype=torch.int32, device="cuda")
+    ctx = api.Context(p)
+    ctx.set_keys(env["bk"], env["ksk"])
+    try:
+        ctx.serve_start(64 << 20)
+        rid = ctx.serve_submit(api.MUL, 16, dev[0], dev[1], out)
+        with pytest.raises(api.TFHEError) as err:
+            ctx.serve_wait(rid, 1)
+        assert err.value.code == -4          # TFHE_ETIMEOUT
+        ctx.serve_wait(rid, 120000)
+        ctx.serve_stop()
+        want, _ = orc.mul(P, env["obk"], env["oksk"], 16, host[0][None], host[1][None])
+        got = out.cpu().numpy().view(np.uint32)[:, :p.n + 1]
+        assert np.array_equal(got, want[0])
+    finally:
+        ctx.close()
