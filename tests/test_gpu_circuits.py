@@ -181,6 +181,27 @@ def test_config1_add32_x256(full):
     assert E.ctx.status() == 0
 
 
+def test_config1_sampled_instances_bit_exact(full):
+    """The bench workload at full parameters (n = 500) and in its launch
+    configuration (one 256-instance schedule, tuned shapes): 16 sampled
+    32-bit additions are recomputed by the oracle gate by gate (154
+    bootstraps each, 62 levels deep) and all 32 output ciphertexts of each
+    are bit-exact."""
+    E = full
+    a, b = synth.int_pairs(256, 32, synth.MASTER_SEED + 1, "add32")
+    da, oa = E.enc_ints(a, 32, synth.MASTER_SEED + 1, "add32a")
+    db, ob = E.enc_ints(b, 32, synth.MASTER_SEED + 1, "add32b")
+    R = E.out((256, 32))
+    E.ctx.add_n(32, da, db, R)
+    got = E.host(R)
+    idx = np.array([0, 1, 17, 40, 63, 64, 99, 127, 128, 150, 191, 200, 222, 240, 254, 255])
+    want, gates = E.orc.add(E.P, E.obk, E.oksk, 32, np.ascontiguousarray(oa[idx]),
+                            np.ascontiguousarray(ob[idx]))
+    assert gates == len(idx) * 154
+    assert np.array_equal(got[idx], want)
+    assert E.ctx.status() == 0
+
+
 def test_config2_mul16_mul32_mixed(full):
     """64 16-bit and 64 32-bit multiplications in one schedule."""
     E = full
