@@ -88,8 +88,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-circuits", default="paper", choices=["paper", "shallow"],
                     help="serving circuits: the paper's ripple-carry adders and shift-and-add "
-                         "multipliers, or majority-carry adders and tree multipliers with "
-                         "majority carries (same results, fewer levels)")
+                         "multipliers, or parallel-prefix adders and Dadda-tree multipliers "
+                         "(same results, fewer levels)")
     ap.add_argument("--variants", action="store_true",
                     help="adder / multiplier variants and the compound-gate ablation")
     ap.add_argument("--configs", action="store_true",
@@ -361,7 +361,8 @@ def run_variants(args):
     a, b = synth.int_pairs(256, 32, seed, "var_add")
     A, B = enc(a, 32, "va"), enc(b, 32, "vb")
     R = torch.empty_like(A)
-    for name, kind in (("ripple", api.ADD), ("majority", api.ADD_MAJ), ("numberwise", api.ADD_NW)):
+    for name, kind in (("ripple", api.ADD), ("majority", api.ADD_MAJ), ("numberwise", api.ADD_NW),
+                       ("prefix", api.ADD_PREFIX)):
         job = [dict(kind=kind, width=32, batch=256, in0=A, in1=B, out=R)]
         ms = timed(lambda: ctx.run_jobs(job), 3)
         g, depth = api.circuit_info(kind, 32)
@@ -374,7 +375,7 @@ def run_variants(args):
     MA, MB = enc(ma, 32, "vma"), enc(mb, 32, "vmb")
     MR = torch.empty_like(MA)
     for name, kind in (("sequential", api.MUL), ("tree", api.MUL_TREE),
-                       ("tree_maj", api.MUL_TREE_MAJ)):
+                       ("tree_maj", api.MUL_TREE_MAJ), ("dadda", api.MUL_DADDA)):
         job = [dict(kind=kind, width=32, batch=64, in0=MA, in1=MB, out=MR)]
         ms = timed(lambda: ctx.run_jobs(job), 2)
         g, depth = api.circuit_info(kind, 32)
@@ -508,9 +509,9 @@ def run_configs(args):
 
 SERVE_KINDS = [("gate", 0, 1), ("add16", 1, 16), ("add32", 1, 32), ("mul16", 2, 16),
                ("mul32", 2, 32)]
-# the same requests with the shallow circuits (ADD_MAJ = 4, MUL_TREE_MAJ = 9)
-SERVE_KINDS_SHALLOW = [("gate", 0, 1), ("add16", 4, 16), ("add32", 4, 32), ("mul16", 9, 16),
-                       ("mul32", 9, 32)]
+# the same requests with the shallow circuits (ADD_PREFIX = 10, MUL_DADDA = 11)
+SERVE_KINDS_SHALLOW = [("gate", 0, 1), ("add16", 10, 16), ("add32", 10, 32), ("mul16", 11, 16),
+                       ("mul32", 11, 32)]
 
 
 def run_serve(args):
@@ -819,9 +820,10 @@ def main():
         latency = measure(api.MUL, args.per_gate_samples)
         latency["request"] = ("one 32x32->32 sequential shift-and-add multiplication "
                               "(2,824 gates, 120 levels) alone")
-        latency_tree = measure(api.MUL_TREE_MAJ, 1)
-        latency_tree["request"] = ("one 32x32->32 multiplication, partial products summed by a "
-                                   "tree of majority-carry adders (1,954 gates, 40 levels) alone")
+        latency_tree = measure(api.MUL_DADDA, 1)
+        latency_tree["request"] = ("one 32x32->32 multiplication, partial products reduced by a "
+                                   "Dadda tree of full adders (majority carries) and summed by a "
+                                   "parallel-prefix adder (2,073 gates, 22 levels) alone")
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
@@ -843,7 +845,7 @@ def main():
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "keyswitch": keyswitch,
                 "cpu_baseline": cpu, "mul32_latency": latency,
-                "mul32_tree_maj_latency": latency_tree, "verified": verified}
+                "mul32_shallow_latency": latency_tree, "verified": verified}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

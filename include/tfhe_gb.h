@@ -200,9 +200,14 @@ typedef enum {
                                /*   split at ceil(w/2), Z2 - (Z0 + Z1) by a       */
                                /*   two's-complement subtractor, the full product */
                                /*   above below 8 bits; 2w bits, 2 <= w <= 64     */
-    TFHE_CIRCUIT_MUL_TREE_MAJ = 9 /* MUL_TREE whose adders carry with majority    */
+    TFHE_CIRCUIT_MUL_TREE_MAJ = 9, /* MUL_TREE whose adders carry with majority   */
                                /*   gates (one MAJ per carry): fewer gates and    */
                                /*   about half the depth, for latency             */
+    TFHE_CIRCUIT_ADD_PREFIX = 10, /* parallel-prefix (Sklansky) adder on majority */
+                               /*   gates, depth ceil(log2(w-1)) + 2, for latency */
+    TFHE_CIRCUIT_MUL_DADDA = 11 /* truncated multiplication by a Dadda tree of    */
+                               /*   full adders (XOR, XOR, MAJ) and half adders   */
+                               /*   and a final ADD_PREFIX: lowest depth          */
 } tfhe_circuit;
 
 typedef struct {

@@ -81,6 +81,8 @@ def lib():
             "orc_add_nw": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_tree": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_tree_maj": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_add_prefix": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
+            "orc_mul_dadda": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_full": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_mul_karatsuba": (i64, [P, vp, vp, i32, i64, vp, vp, vp, i32]),
             "orc_blind_rotate_many": (None, [P, vp, i64, vp, u32, vp, i32]),
@@ -279,6 +281,16 @@ def mul_tree(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
 def mul_tree_maj(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
     """Tree-accumulated multiplication with majority-carry adders -> (R, gates)."""
     return _circuit("orc_mul_tree_maj", P, bk, ksk, w, A, B, nthreads)
+
+
+def add_prefix(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Sklansky parallel-prefix adder (majority gates) -> (R, gates)."""
+    return _circuit("orc_add_prefix", P, bk, ksk, w, A, B, nthreads)
+
+
+def mul_dadda(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
+    """Truncated multiplication by a Dadda tree and a prefix adder -> (R, gates)."""
+    return _circuit("orc_mul_dadda", P, bk, ksk, w, A, B, nthreads)
 
 
 def _full(name, P, bk, ksk, w, A, B, nthreads):

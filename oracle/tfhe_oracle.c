@@ -747,6 +747,218 @@ static void ev_mul_tree_maj(orc_ev *E, int32_t w, const uint32_t *Av, const uint
     ev_mul_tree_with(E, w, Av, Bv, R, 1);
 }
 
+/* Sklansky parallel-prefix addition of wire vectors (NULL = constant 0),
+ * w bits mod 2^w, with majority gates.  Per bit i: g_i = x_i AND y_i (bits
+ * below w-1: there is no carry out), k_i = x_i OR y_i (bits 1 .. w-2: the
+ * group holding bit 0 never needs K) and p_i = x_i XOR y_i; with one operand
+ * the constant 0, g_i = 0 and k_i, p_i are the other operand.  For a group of bits, G says it produces a carry
+ * and K says it produces or passes one (G implies K); putting a high group
+ * on top of a low one gives G = MAJ(G_hi, K_hi, G_lo) and
+ * K = MAJ(G_hi, K_hi, K_lo), since G_hi OR (K_hi AND L) is the majority of
+ * the three when G_hi implies K_hi.  For span = 1, 2, 4, ... while
+ * span < w - 1, every bit i <= w - 2 in the upper half of its block of
+ * 2 span bits takes in the group ending at the lower half's top bit j; K is
+ * updated only where the merged group does not reach bit 0 (i >= 2 span).
+ * A merge with a constant-0 low signal or K_hi keeps G_hi; with G_hi the
+ * constant 0 it is K_hi AND low.  Then s_0 = p_0 and s_i = p_i XOR G_(i-1),
+ * without a gate when one side is the constant 0.  This is the gate list
+ * the CUDA library's netlist builds (the circuit is defined gate for gate). */
+static const uint32_t *ev_merge(orc_ev *E, orc_arena *A, const uint32_t *g_hi,
+                                const uint32_t *k_hi, const uint32_t *lo)
+{
+    if (!lo || !k_hi)
+        return g_hi;
+    uint32_t *o = arena_new(A);
+    if (!g_hi) {
+        ev_gate(E, ORC_AND, k_hi, lo, o);
+    } else {
+        orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, g_hi, k_hi, lo, o);
+        E->gates++;
+    }
+    return o;
+}
+
+static void ev_prefix_cells(orc_ev *E, orc_arena *A, int32_t w, const uint32_t **x,
+                            const uint32_t **y, const uint32_t **s)
+{
+    const uint32_t **g = calloc(w, sizeof(*g)), **kk = calloc(w, sizeof(*kk));
+    const uint32_t **bitp = calloc(w, sizeof(*bitp));
+    const uint32_t **ng = calloc(w, sizeof(*ng)), **nk = calloc(w, sizeof(*nk));
+    for (int32_t i = 0; i < w; i++) {
+        if (x[i] && y[i]) {
+            if (i < w - 1) {
+                uint32_t *o1 = arena_new(A);
+                ev_gate(E, ORC_AND, x[i], y[i], o1);
+                g[i] = o1;
+            }
+            if (i > 0 && i < w - 1) {
+                uint32_t *o2 = arena_new(A);
+                ev_gate(E, ORC_OR, x[i], y[i], o2);
+                kk[i] = o2;
+            }
+            uint32_t *o = arena_new(A);
+            ev_gate(E, ORC_XOR, x[i], y[i], o);
+            bitp[i] = o;
+        } else {
+            bitp[i] = x[i] ? x[i] : y[i];
+            if (i < w - 1)
+                kk[i] = bitp[i];
+        }
+    }
+    for (int32_t span = 1; span < w - 1; span *= 2) {
+        memcpy(ng, g, sizeof(*g) * w);
+        memcpy(nk, kk, sizeof(*kk) * w);
+        for (int32_t i = 0; i <= w - 2; i++) {
+            if ((i / span) % 2 == 0)
+                continue;                               /* lower half: unchanged */
+            const int32_t j = (i / (2 * span)) * (2 * span) + span - 1;
+            ng[i] = ev_merge(E, A, g[i], kk[i], g[j]);
+            if (i >= 2 * span)
+                nk[i] = ev_merge(E, A, g[i], kk[i], kk[j]);
+        }
+        memcpy(g, ng, sizeof(*g) * w);
+        memcpy(kk, nk, sizeof(*kk) * w);
+    }
+    for (int32_t i = 0; i < w; i++) {
+        const uint32_t *c = i > 0 ? g[i - 1] : NULL;
+        if (!c) {
+            s[i] = bitp[i];
+        } else if (!bitp[i]) {
+            s[i] = c;
+        } else {
+            uint32_t *o = arena_new(A);
+            ev_gate(E, ORC_XOR, bitp[i], c, o);
+            s[i] = o;
+        }
+    }
+    free(g); free(kk); free(bitp); free(ng); free(nk);
+}
+
+static void ev_add_prefix(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
+                          uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    orc_arena A = {NULL, 0, 0, W};
+    const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
+                   **r = malloc(sizeof(*r) * w);
+    for (int32_t i = 0; i < w; i++) {
+        x[i] = Av + i * W;
+        y[i] = Bv + i * W;
+    }
+    ev_prefix_cells(E, &A, w, x, y, r);
+    copy_out(w, W, r, R);
+    free(x); free(y); free(r);
+    arena_free(&A);
+}
+
+/* Truncated w x w -> w multiplication by a Dadda tree.  Column c (weight
+ * 2^c) begins with the partial products a_(c-i) AND b_i, i = 0 .. c, in that
+ * order.  The stage targets are the numbers 2, 3, 4, 6, 9, 13, ... (each
+ * the floor of 3/2 times the one before) below w, used from the largest
+ * down.  A stage with target d walks the columns from c = 0 up; the height
+ * of column c is its own wires plus the carries column c - 1 has already
+ * sent it in this stage.  While the height exceeds d, the column's oldest
+ * unused wires go into a half adder (sum u XOR v, carry u AND v) if the
+ * height is d + 1, else into a full adder (sum (u XOR v) XOR z, carry
+ * MAJ(u, v, z)); sums stay in column c, carries go to column c + 1 (none is
+ * formed out of column w - 1).  The column's next contents are the carries
+ * it received, its sums, then its unused wires, in that order.  The two
+ * rows left are added by the parallel-prefix adder above.  Returns -1 if a
+ * column runs out of wires (not the case for w <= 64). */
+static int ev_mul_dadda_impl(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
+                             uint32_t *R)
+{
+    const int64_t W = E->P->n + 1;
+    const int32_t cap = 2 * w + 8;
+    orc_arena A = {NULL, 0, 0, W};
+    const uint32_t **col = malloc(sizeof(*col) * w * cap), **nxt = malloc(sizeof(*nxt) * w * cap);
+    int32_t *len = calloc(w, sizeof(int32_t)), *nlen = calloc(w, sizeof(int32_t));
+    int32_t target[16], nt = 0, ok = 0;
+    for (int32_t c = 0; c < w; c++)
+        for (int32_t i = 0; i <= c; i++) {
+            uint32_t *o = arena_new(&A);
+            ev_gate(E, ORC_AND, Av + (c - i) * W, Bv + i * W, o);
+            col[c * cap + len[c]++] = o;
+        }
+    for (int32_t d = 2; d < w; d = d * 3 / 2)
+        target[nt++] = d;
+    for (int32_t t = nt - 1; t >= 0; t--) {
+        const int32_t d = target[t];
+        memset(nlen, 0, sizeof(int32_t) * w);
+        for (int32_t c = 0; c < w; c++) {
+            int32_t used = 0, h = len[c] + nlen[c];
+            while (h > d) {
+                const int32_t need = h == d + 1 ? 2 : 3;
+                if (used + need > len[c])
+                    goto done;
+                const uint32_t *u = col[c * cap + used], *v = col[c * cap + used + 1];
+                uint32_t *sum = arena_new(&A);
+                if (need == 2) {
+                    ev_gate(E, ORC_XOR, u, v, sum);
+                    if (c + 1 < w) {
+                        uint32_t *cy = arena_new(&A);
+                        ev_gate(E, ORC_AND, u, v, cy);
+                        nxt[(c + 1) * cap + nlen[c + 1]++] = cy;
+                    }
+                    h -= 1;
+                } else {
+                    const uint32_t *z = col[c * cap + used + 2];
+                    uint32_t *uv = arena_new(&A);
+                    ev_gate(E, ORC_XOR, u, v, uv);
+                    ev_gate(E, ORC_XOR, uv, z, sum);
+                    if (c + 1 < w) {
+                        uint32_t *cy = arena_new(&A);
+                        orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, u, v, z, cy);
+                        E->gates++;
+                        nxt[(c + 1) * cap + nlen[c + 1]++] = cy;
+                    }
+                    h -= 2;
+                }
+                nxt[c * cap + nlen[c]++] = sum;
+                used += need;
+            }
+            for (; used < len[c]; used++)
+                nxt[c * cap + nlen[c]++] = col[c * cap + used];
+        }
+        const uint32_t **tmp = col;
+        col = nxt;
+        nxt = tmp;
+        int32_t *tl = len;
+        len = nlen;
+        nlen = tl;
+    }
+    {
+        const uint32_t **x = calloc(w, sizeof(*x)), **y = calloc(w, sizeof(*y)),
+                       **r = malloc(sizeof(*r) * w);
+        int32_t fits = 1;
+        for (int32_t c = 0; c < w; c++) {
+            if (len[c] > 2)
+                fits = 0;
+            if (len[c] > 0)
+                x[c] = col[c * cap];
+            if (len[c] > 1)
+                y[c] = col[c * cap + 1];
+        }
+        if (fits) {
+            ev_prefix_cells(E, &A, w, x, y, r);
+            copy_out(w, W, r, R);
+            ok = 1;
+        }
+        free(x); free(y); free(r);
+    }
+done:
+    free(col); free(nxt); free(len); free(nlen);
+    arena_free(&A);
+    return ok ? 0 : -1;
+}
+
+static void ev_mul_dadda(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
+                         uint32_t *R)
+{
+    if (ev_mul_dadda_impl(E, w, Av, Bv, R) != 0)
+        memset(R, 0, sizeof(uint32_t) * (E->P->n + 1) * w);
+}
+
 /* Full product Z = X Y of n-bit X, Y as 2n bits (section III-B-1, "Naive
  * Approach", without truncation): partial product i is X AND y_i moved up by
  * i bits, so it covers weights i .. i+n-1 of the 2n; the n partial products
@@ -1014,6 +1226,20 @@ int64_t orc_mul_tree_maj(const orc_params *P, const uint32_t *bk, const uint32_t
                      int32_t nthreads)
 {
     return run_batched(ev_mul_tree_maj, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_add_prefix(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                     int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                     int32_t nthreads)
+{
+    return run_batched(ev_add_prefix, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_mul_dadda(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                     int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R,
+                     int32_t nthreads)
+{
+    return run_batched(ev_mul_dadda, P, bk, ksk, w, batch, A, B, R, nthreads);
 }
 
 int64_t orc_matvec(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,

@@ -98,7 +98,8 @@ EXPORTS = {
                    + [ctypes.c_size_t, ctypes.c_void_p]),
 }
 
-GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA, MUL_TREE_MAJ = range(10)
+GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA, MUL_TREE_MAJ, \
+    ADD_PREFIX, MUL_DADDA = range(12)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH, \
     OPT_KS_KERNEL, OPT_TEST_KS_STALL = range(8)
 KS_TILED = 64   # OPT_KS_KERNEL value of the tiled key-switch kernel

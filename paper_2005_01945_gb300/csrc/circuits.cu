@@ -174,6 +174,137 @@ static std::vector<int> build_mul_tree(Netlist &nl, const std::vector<int> &x,
     return terms[0];
 }
 
+// Parallel-prefix adder (Sklansky): the w-bit sum mod 2^w of wire vectors
+// with constant-zero entries (-1), on majority gates only.  Bit i gives
+// generate g_i = x_i AND y_i (i < w - 1: there is no carry out),
+// carry-or-transmit k_i = x_i OR y_i (0 < i < w - 1: a group that starts
+// at bit 0 never needs its K) and p_i = x_i XOR y_i for its sum.  A group of bits has generate G (it makes a carry) and K = G OR
+// (every bit transmits), so G implies K and the merge of a high group with
+// the low group below it is two majority gates:
+//   G = G_hi OR (K_hi AND G_lo) = MAJ(G_hi, K_hi, G_lo),
+//   K = G_hi OR (K_hi AND K_lo) = MAJ(G_hi, K_hi, K_lo).
+// Prefix level k (while 2^k < w - 1) merges, for every bit i <= w - 2 with
+// bit k set, the group ending at i with the one ending at
+// j = (i with its low k + 1 bits cleared) + 2^k - 1; K is formed only where
+// the merged group does not start at bit 0.  The sum is
+// s_i = p_i XOR G_(i-1) (s_0 = p_0).  Constant zeros are folded (a merge
+// with G_lo = 0 keeps G_hi; with G_hi = 0 it is K_hi AND G_lo), so no gate
+// gets a constant input.  Every gate keeps the 1/8 margin of the majority
+// and two-input gates.
+static std::vector<int> build_add_prefix(Netlist &nl, const std::vector<int> &x,
+                                         const std::vector<int> &y)
+{
+    const int w = (int)x.size();
+    std::vector<int> G(w, -1), K(w, -1), p(w, -1);
+    for (int i = 0; i < w; ++i) {
+        if (x[i] >= 0 && y[i] >= 0) {
+            if (i + 1 < w)
+                G[i] = nl.gate(TFHE_AND, x[i], y[i]);
+            if (i > 0 && i + 1 < w)
+                K[i] = nl.gate(TFHE_OR, x[i], y[i]);
+            p[i] = nl.gate(TFHE_XOR, x[i], y[i]);
+        } else {
+            p[i] = x[i] >= 0 ? x[i] : y[i];
+            if (i + 1 < w)
+                K[i] = p[i];
+        }
+    }
+    // G_hi OR (K_hi AND L), folding constant zeros
+    auto merge = [&nl](int g_hi, int k_hi, int lo) {
+        if (lo < 0 || k_hi < 0)
+            return g_hi;
+        if (g_hi < 0)
+            return nl.gate(TFHE_AND, k_hi, lo);
+        return nl.gate(TFHE_MAJ, g_hi, k_hi, lo);
+    };
+    for (int k = 0; (1 << k) < w - 1; ++k) {
+        std::vector<int> nG(G), nK(K);
+        for (int i = 0; i <= w - 2; ++i) {
+            if (!((i >> k) & 1))
+                continue;
+            const int j = ((i >> (k + 1)) << (k + 1)) + (1 << k) - 1;
+            nG[i] = merge(G[i], K[i], G[j]);
+            if ((i >> (k + 1)) != 0)
+                nK[i] = merge(G[i], K[i], K[j]);
+        }
+        G.swap(nG);
+        K.swap(nK);
+    }
+    std::vector<int> s(w);
+    for (int i = 0; i < w; ++i) {
+        const int c = i ? G[i - 1] : -1;
+        s[i] = c < 0 ? p[i] : p[i] < 0 ? c : nl.gate(TFHE_XOR, p[i], c);
+    }
+    return s;
+}
+
+// Truncated multiplication (w x w -> w bits) by a Dadda tree.  Column c
+// starts with the partial products a_(c-i) AND b_i, i = 0 .. c.  Stage
+// targets are the terms of d_1 = 2, d_(k+1) = floor(3 d_k / 2) below w,
+// largest first.  In a stage every column, in increasing order, is reduced
+// to at most d wires, its height counting the carries the previous column
+// sent it in this stage: a half adder (sum x XOR y, carry x AND y) when one
+// wire too many, else a full adder (sum (x XOR y) XOR z, carry MAJ(x, y, z)),
+// on the column's oldest wires.  The new column lists the carries received,
+// then its sums, then its untouched wires.  Carries out of column w - 1 are
+// not built.  The two rows left go to the parallel-prefix adder.  Returns
+// false if a column lacks wires for its adders (no width up to 64 does).
+static bool build_mul_dadda(Netlist &nl, const std::vector<int> &x, const std::vector<int> &y,
+                            std::vector<int> &out)
+{
+    const int w = (int)x.size();
+    std::vector<std::vector<int>> col(w);
+    for (int c = 0; c < w; ++c)
+        for (int i = 0; i <= c; ++i)
+            col[c].push_back(nl.gate(TFHE_AND, x[c - i], y[i]));
+    std::vector<int> targets;
+    for (int d = 2; d < w; d = d * 3 / 2)
+        targets.push_back(d);
+    for (auto t = targets.rbegin(); t != targets.rend(); ++t) {
+        const int d = *t;
+        std::vector<std::vector<int>> nc(w);
+        for (int c = 0; c < w; ++c) {
+            const std::vector<int> &L = col[c];
+            size_t pos = 0;
+            int h = (int)(L.size() + nc[c].size());
+            while (h > d) {
+                const bool half = h - d == 1;
+                if (pos + (half ? 2 : 3) > L.size())
+                    return false;
+                const int u = L[pos], v = L[pos + 1];
+                if (half) {
+                    nc[c].push_back(nl.gate(TFHE_XOR, u, v));
+                    if (c + 1 < w)
+                        nc[c + 1].push_back(nl.gate(TFHE_AND, u, v));
+                    pos += 2;
+                    h -= 1;
+                } else {
+                    const int z = L[pos + 2];
+                    nc[c].push_back(nl.gate(TFHE_XOR, nl.gate(TFHE_XOR, u, v), z));
+                    if (c + 1 < w)
+                        nc[c + 1].push_back(nl.gate(TFHE_MAJ, u, v, z));
+                    pos += 3;
+                    h -= 2;
+                }
+            }
+            for (; pos < L.size(); ++pos)
+                nc[c].push_back(L[pos]);
+        }
+        col.swap(nc);
+    }
+    std::vector<int> r0(w, -1), r1(w, -1);
+    for (int c = 0; c < w; ++c) {
+        if (col[c].size() > 2)
+            return false;
+        if (col[c].size() > 0)
+            r0[c] = col[c][0];
+        if (col[c].size() > 1)
+            r1[c] = col[c][1];
+    }
+    out = build_add_prefix(nl, r0, r1);
+    return true;
+}
+
 // Full product of two wire vectors (len(x) = len(y) = n -> 2n bits):
 // partial products at their weights, summed by the same pairwise tree.
 static std::vector<int> build_mul_full(Netlist &nl, const std::vector<int> &x,
@@ -321,6 +452,19 @@ bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
                      ? build_add_numberwise(nl, range_wires(0, w), range_wires(w, w))
                      : build_mul_tree(nl, range_wires(0, w), range_wires(w, w),
                                       kind == TFHE_CIRCUIT_MUL_TREE_MAJ);
+        for (int o : nl.out)
+            if (o < 0)
+                return false;
+        break;
+    case TFHE_CIRCUIT_ADD_PREFIX:
+    case TFHE_CIRCUIT_MUL_DADDA:
+        if (w < 1 || w > 64)
+            return false;
+        nl.n_in = 2 * w;
+        if (kind == TFHE_CIRCUIT_ADD_PREFIX)
+            nl.out = build_add_prefix(nl, range_wires(0, w), range_wires(w, w));
+        else if (!build_mul_dadda(nl, range_wires(0, w), range_wires(w, w), nl.out))
+            return false;
         for (int o : nl.out)
             if (o < 0)
                 return false;

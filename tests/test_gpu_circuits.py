@@ -202,6 +202,28 @@ def test_config1_sampled_instances_bit_exact(full):
     assert E.ctx.status() == 0
 
 
+def test_shallow_circuits_full_parameters_decrypt(full):
+    """The low-depth circuits at n = 500: 256 parallel-prefix additions and
+    64 Dadda multiplications of 32 bits (197K bootstraps, mostly majority
+    gates) in one schedule; every output decrypts to the integer result.
+    Bit-exact parity at n = 16 cannot see the noise, so this checks that
+    every gate of these circuits keeps its decision margin."""
+    E = full
+    api = E.api
+    a, b = synth.int_pairs(256, 32, 81, "px")
+    c, d = synth.int_pairs(64, 32, 82, "dd")
+    da, _ = E.enc_ints(a, 32, 81, "pxa")
+    db, _ = E.enc_ints(b, 32, 81, "pxb")
+    dc, _ = E.enc_ints(c, 32, 82, "dda")
+    dd, _ = E.enc_ints(d, 32, 82, "ddb")
+    R1, R2 = E.out((256, 32)), E.out((64, 32))
+    E.ctx.run_jobs([dict(kind=api.ADD_PREFIX, width=32, batch=256, in0=da, in1=db, out=R1),
+                    dict(kind=api.MUL_DADDA, width=32, batch=64, in0=dc, in1=dd, out=R2)])
+    assert np.array_equal(E.dec_ints(E.host(R1)), (a + b) % (1 << 32))
+    assert np.array_equal(E.dec_ints(E.host(R2)), (c * d) % (1 << 32))
+    assert E.ctx.status() == 0
+
+
 def test_config2_mul16_mul32_mixed(full):
     """64 16-bit and 64 32-bit multiplications in one schedule."""
     E = full
@@ -239,10 +261,12 @@ def test_config3_matvec16(full):
 
 @pytest.mark.parametrize("kind_name,w", [("ADD_MAJ", 32), ("ADD_NW", 8), ("MUL_TREE", 8),
                                          ("ADD_MAJ", 1), ("MUL_TREE", 3), ("MUL_TREE_MAJ", 8),
-                                         ("MUL_TREE_MAJ", 5)])
+                                         ("MUL_TREE_MAJ", 5), ("ADD_PREFIX", 32), ("ADD_PREFIX", 6),
+                                         ("MUL_DADDA", 8), ("MUL_DADDA", 6)])
 def test_next_circuits_bit_exact(small, kind_name, w):
-    """Majority-carry adder (3-input MAJ gates), the paper's number-wise adder
-    and tree-accumulated multiplication (ripple or majority carries),
+    """Majority-carry adder (3-input MAJ gates), the paper's number-wise
+    adder, tree-accumulated multiplication (ripple or majority carries), the
+    parallel-prefix adder (majority gates) and the Dadda multiplier,
     bit-exact against the oracle."""
     E = small
     api = E.api
@@ -253,7 +277,8 @@ def test_next_circuits_bit_exact(small, kind_name, w):
     R = E.out((2, w))
     E.ctx.run_jobs([dict(kind=kind, width=w, batch=2, in0=da, in1=db, out=R)])
     fn = {"ADD_MAJ": E.orc.add_maj, "ADD_NW": E.orc.add_nw, "MUL_TREE": E.orc.mul_tree,
-          "MUL_TREE_MAJ": E.orc.mul_tree_maj}[kind_name]
+          "MUL_TREE_MAJ": E.orc.mul_tree_maj, "ADD_PREFIX": E.orc.add_prefix,
+          "MUL_DADDA": E.orc.mul_dadda}[kind_name]
     want, g = fn(E.P, E.obk, E.oksk, w, oa, ob)
     got = E.host(R)
     assert np.array_equal(got, want)

@@ -144,12 +144,14 @@ def test_balanced_schedule_invariants():
     assert (wb[:-1] == 608).all() and wb[-1] == 39424 - 61 * 608
 
 
-@pytest.mark.parametrize("name", ["add_maj", "add_nw", "mul_tree", "mul_tree_maj"])
+@pytest.mark.parametrize("name", ["add_maj", "add_nw", "mul_tree", "mul_tree_maj", "add_prefix",
+                                  "mul_dadda"])
 @pytest.mark.parametrize("w", [1, 2, 3, 4])
 def test_new_circuits_exhaustive(orc, toy, name, w):
-    """Majority-carry adder, the paper's number-wise adder GPU_n and
-    tree-accumulated multiplication (ripple or majority carries): every
-    input pair at toy parameters."""
+    """Majority-carry adder, the paper's number-wise adder GPU_n,
+    tree-accumulated multiplication (ripple or majority carries), the
+    parallel-prefix adder and the Dadda multiplier: every input pair at toy
+    parameters."""
     p, P, kd, bk, ksk = toy
     a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
     a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
@@ -157,6 +159,22 @@ def test_new_circuits_exhaustive(orc, toy, name, w):
                               _enc_ints(orc, p, P, kd, b, w, f"{name}b{w}"))
     want = (a * b if name.startswith("mul") else a + b) % (1 << w)
     assert np.array_equal(_dec_ints(orc, P, kd, R), want)
+
+
+@pytest.mark.parametrize("w", [5, 6])
+def test_prefix_adder_and_dadda_exhaustive_w5_w6(orc, toy, w):
+    """Parallel-prefix adder and Dadda multiplier at widths where the prefix
+    network has 3 and 3 levels with ragged blocks (w - 1 = 4, 5) and the
+    Dadda tree 2 and 3 stages: every input pair at toy parameters."""
+    p, P, kd, bk, ksk = toy
+    a, b = np.meshgrid(np.arange(1 << w), np.arange(1 << w), indexing="ij")
+    a, b = a.ravel().astype(np.uint64), b.ravel().astype(np.uint64)
+    A = _enc_ints(orc, p, P, kd, a, w, f"pxa{w}")
+    B = _enc_ints(orc, p, P, kd, b, w, f"pxb{w}")
+    R, _ = orc.add_prefix(P, bk, ksk, w, A, B)
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a + b) % (1 << w))
+    R, _ = orc.mul_dadda(P, bk, ksk, w, A, B)
+    assert np.array_equal(_dec_ints(orc, P, kd, R), (a * b) % (1 << w))
 
 
 @pytest.mark.parametrize("w", [8, 16, 32])
@@ -172,7 +190,9 @@ def test_new_circuits_wide_and_counts(orc, toy, w):
     for name, kind, want in (("add_maj", api.ADD_MAJ, (a + b) % (1 << w)),
                              ("add_nw", api.ADD_NW, (a + b) % (1 << w)),
                              ("mul_tree", api.MUL_TREE, (a * b) % (1 << w)),
-                             ("mul_tree_maj", api.MUL_TREE_MAJ, (a * b) % (1 << w))):
+                             ("mul_tree_maj", api.MUL_TREE_MAJ, (a * b) % (1 << w)),
+                             ("add_prefix", api.ADD_PREFIX, (a + b) % (1 << w)),
+                             ("mul_dadda", api.MUL_DADDA, (a * b) % (1 << w))):
         R, g = getattr(orc, name)(P, bk, ksk, w, A, B)
         assert np.array_equal(_dec_ints(orc, P, kd, R), want), name
         assert g == 3 * api.circuit_info(kind, w)[0], name
