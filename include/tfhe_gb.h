@@ -101,6 +101,18 @@ int tfhe_ctx_set_keys(tfhe_ctx *ctx, const int32_t *bk, const int32_t *ksk, void
 
 void tfhe_ctx_destroy(tfhe_ctx *ctx);
 
+/* Save the context's device keys to a file, and load them into a context of
+ * the same parameters (no counterpart in the paper: checkpoint / resume of a
+ * serving process).  The file holds the keys as the context keeps them (the
+ * bootstrapping key already in the NTT domain of this library's primes) after
+ * a header with the parameters, the primes, the sizes and a 64-bit checksum;
+ * loading returns TFHE_EINVAL for another library's file, other parameters, a
+ * short file or a checksum mismatch, and leaves the context's keys as they
+ * were.  Both are synchronous (device <-> host copies on the legacy stream);
+ * saving needs keys set. */
+int tfhe_ctx_save_keys(tfhe_ctx *ctx, const char *path);
+int tfhe_ctx_load_keys(tfhe_ctx *ctx, const char *path);
+
 /* Last error message of the context (NUL-terminated, truncated to len). */
 int tfhe_last_error(const tfhe_ctx *ctx, char *buf, size_t len);
 

@@ -47,6 +47,8 @@ EXPORTS = {
     "tfhe_ctx_create": (ctypes.c_int, [ctypes.POINTER(CParams), ctypes.c_int, ctypes.c_void_p]),
     "tfhe_ctx_set_keys": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "tfhe_ctx_destroy": (None, [ctypes.c_void_p]),
+    "tfhe_ctx_save_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "tfhe_ctx_load_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "tfhe_last_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "tfhe_ctx_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "tfhe_bootstrap_gates": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t, ctypes.c_void_p]),
@@ -207,6 +209,15 @@ class Context:
     def set_keys(self, bk, ksk, stream=None):
         """bk int32 [n][4][2][N], ksk int32 [N][t][3][n+1]; host or device."""
         self._c(lib().tfhe_ctx_set_keys(self._h, _ptr(bk), _ptr(ksk), _stream(stream)))
+
+    def save_keys(self, path):
+        """Write the device keys (NTT-domain bootstrapping key, padded
+        key-switching key) with a checked header to `path`."""
+        self._c(lib().tfhe_ctx_save_keys(self._h, os.fsencode(path)))
+
+    def load_keys(self, path):
+        """Load keys written by save_keys for the same parameters."""
+        self._c(lib().tfhe_ctx_load_keys(self._h, os.fsencode(path)))
 
     def status(self) -> int:
         code = ctypes.c_uint32(0)

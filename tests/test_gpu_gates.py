@@ -181,6 +181,52 @@ def test_keyswitch_kernels_agree_on_gates(gpu, orc):
     assert torch.equal(outs[0], outs[1])
 
 
+def test_keys_save_and_load(gpu, orc, tmp_path):
+    """Checkpoint / resume of the device keys: a new context loads the file
+    the first one saved and gives the same gates (bit-exact against the
+    oracle); a flipped payload byte, keys of other parameters and a missing
+    file are refused with TFHE_EINVAL."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    path = tmp_path / "keys.tfhegb"
+    gpu["ctx"].save_keys(path)
+    count = 9
+    bits, cts, dev = _fresh(gpu, orc, count, 88, "keyio")
+    ops = (np.arange(count) % 6).astype(np.uint8)
+    ctx2 = api.Context(p)
+    try:
+        ctx2.load_keys(path)
+        outs = []
+        for ctx in (gpu["ctx"], ctx2):
+            out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+            ctx.bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+            outs.append(out)
+        assert torch.equal(outs[0], outs[1])
+        want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
+        assert np.array_equal(_u32(outs[1])[:, :p.n + 1], want)
+        bad = tmp_path / "bad.tfhegb"
+        raw = bytearray(path.read_bytes())
+        raw[len(raw) // 2] ^= 1
+        bad.write_bytes(bytes(raw))
+        with pytest.raises(api.TFHEError) as err:
+            ctx2.load_keys(bad)
+        assert err.value.code == -1
+        with pytest.raises(api.TFHEError):
+            ctx2.load_keys(tmp_path / "missing.tfhegb")
+        # the refused loads left the loaded keys in place
+        out = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+        ctx2.bootstrap_gates(api.to_device(ops), dev[0], dev[1], out)
+        assert torch.equal(out, outs[0])
+    finally:
+        ctx2.close()
+    ctx3 = api.Context(synth.TFHEParams(n=16))
+    try:
+        with pytest.raises(api.TFHEError) as err:
+            ctx3.load_keys(path)
+        assert err.value.code == -1
+    finally:
+        ctx3.close()
+
+
 def test_trivial_keys_exact_rotation_large_batch(orc):
     """Zero-mask, zero-noise bootstrapping key: after blind rotation the
     extracted sample is exactly (0, coefficient 0 of X^m v) for every gate of
