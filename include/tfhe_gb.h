@@ -7,9 +7,10 @@
  * key), and the boolean circuits the paper builds from them: ripple-carry
  * addition (Eq. "addres", Eq. "addcarry"; sections III-A and V-B-1),
  * shift-and-add multiplication (section III-B-1) and the matrix-vector
- * product with tree accumulation (sections IV-D and V-B-2).  Independent
- * gates of a circuit level run together in one batched launch (the paper's
- * bit coalescing and compound gates, section V-A).
+ * product with tree accumulation (sections IV-D and V-B-2), with variants
+ * of lower depth (majority-carry, parallel-prefix and Dadda circuits).
+ * Independent gates of a circuit level run together in one batched launch
+ * (the paper's bit coalescing and compound gates, section V-A).
  *
  * Conventions used by every entry point:
  *   - Torus32: a torus element x/2^32 is stored as one 32-bit word.
@@ -129,8 +130,9 @@ int tfhe_ctx_status(tfhe_ctx *ctx, uint32_t *code);
 
 /* count independent bootstrapped gates: out[g] = ops[g](a[g], b[g]).
  * ops: uint8 [count] device; a, b, out: [count][TFHE_LWE_STRIDE] device.
- * The batch runs as one blind-rotation launch and one key-switch launch.
- * count == 0 is a no-op. */
+ * The batch runs as one blind-rotation launch and one key switch (one
+ * kernel, or two when the j-range is split and the output rows are
+ * initialised first).  count == 0 is a no-op. */
 int tfhe_bootstrap_gates(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int32_t *b,
                          int32_t *out, size_t count, void *stream);
 
