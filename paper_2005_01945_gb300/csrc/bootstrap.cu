@@ -73,10 +73,11 @@ struct Prime {
     uint32_t q, q2, P;
     __device__ __forceinline__ explicit Prime(uint32_t p)
         : q(p ? kQ1 : kQ0), q2(2 * (p ? kQ1 : kQ0)), P(p) {}
-    // K q for K in {1, 2, 4, 8, 16} (16 q < 2^32 for both primes)
+    // K q for K in {1, 2, 4, 8, 16, 32} (32 q < 2^32 for both primes)
     __device__ __forceinline__ uint32_t kq(int K) const
     {
-        return K == 1 ? q : K == 2 ? q2 : K == 4 ? q2 << 1 : K == 8 ? q2 << 2 : q2 << 3;
+        return K == 1 ? q : K == 2 ? q2 : K == 4 ? q2 << 1 : K == 8 ? q2 << 2
+             : K == 16 ? q2 << 3 : q2 << 4;
     }
 };
 
@@ -85,7 +86,8 @@ struct Prime {
 // known at compile time; a reduction csub(x, K q) (valid for b <= 2K)
 // leaves [0, K q).  LazyPlan walks the 80 butterflies of a 32-point pass
 // in the same order as the code and places the fewest reductions that keep
-// every sum below thr q (<= 16 q < 2^32), and the final outputs below fin q:
+// every sum below thr q (<= kLazyMax q < 2^32), and the final outputs below
+// fin q:
 //  * CT butterfly (u, v) -> (u + t, u - t + K' q), t = v (trivial twiddle)
 //    or Shoup(v) in [0, 2q), K' >= bound(t) the smallest power of two;
 //  * GS butterfly (u, v) -> (u + v, d), d = u - v + K' q (K' >= bound(v)),
@@ -104,13 +106,19 @@ struct LazyPlan {
     bool ok;
 };
 
-__host__ __device__ constexpr int lazy_off(int b) { return b <= 1 ? 1 : b <= 2 ? 2 : b <= 4 ? 4 : b <= 8 ? 8 : 16; }
+constexpr int kLazyMax = 32;   // every lazy value stays below 32 q < 2^32
 
-// One reduction step of a value with bound b: the smallest K in {1, 2, 4, 8}
-// with 2K >= b; returns the new bound (or b if none applies).
+__host__ __device__ constexpr int lazy_off(int b)
+{
+    return b <= 1 ? 1 : b <= 2 ? 2 : b <= 4 ? 4 : b <= 8 ? 8 : b <= 16 ? 16 : 32;
+}
+
+// One reduction step of a value with bound b: the smallest K in
+// {1, 2, 4, 8, 16} with 2K >= b; returns the new bound (or b if none
+// applies).
 __host__ __device__ constexpr int lazy_step(int b, int &K)
 {
-    K = b <= 2 ? 1 : b <= 4 ? 2 : b <= 8 ? 4 : b <= 16 ? 8 : 0;
+    K = b <= 2 ? 1 : b <= 4 ? 2 : b <= 8 ? 4 : b <= 16 ? 8 : b <= 32 ? 16 : 0;
     if (K == 0 || K >= b)
         return b;
     return K > b - K ? K : b - K;
@@ -134,7 +142,7 @@ __host__ __device__ constexpr LazyPlan make_lazy_plan(bool ct, bool trivial_firs
                 int bu = b[j], bv = b[j + ln];
                 for (int guard = 0; guard < 8; ++guard) {
                     const int bt = (ct && !triv) ? 2 : bv;
-                    if (bu + bt <= thr && bu + lazy_off(bt) <= 16)
+                    if (bu + bt <= thr && bu + lazy_off(bt) <= kLazyMax)
                         break;
                     int K = 0;
                     if ((!ct || triv) && bt >= bu) {
@@ -159,7 +167,7 @@ __host__ __device__ constexpr LazyPlan make_lazy_plan(bool ct, bool trivial_firs
                     b[j] = bu + bv;
                     b[j + ln] = triv ? bu + L.off : 2;
                 }
-                if (b[j] > 16 || b[j + ln] > 16)
+                if (b[j] > kLazyMax || b[j + ln] > kLazyMax)
                     P.ok = false;
             }
         }
@@ -179,17 +187,18 @@ __host__ __device__ constexpr LazyPlan make_lazy_plan(bool ct, bool trivial_firs
 
 // Forward passes: stage A (negacyclic twiddles, inputs [0, 2q), outputs
 // < 12q, no reduction needed) and stage D (cyclic, the first twiddle of
-// every level is 1; inputs [0, 2q), outputs [0, 4q) for the pointwise
+// every level is 1; inputs [0, 2q), outputs [0, 8q) for the pointwise
 // products).  Inverse passes: stage D' (cyclic GS, inputs [0, 2q) from the
-// pointwise Montgomery step, outputs < 16q into the Shoup twiddle) and
-// stage A' (negacyclic GS, inputs [0, 2q), outputs [0, 2q)).
-constexpr LazyPlan kPlanFwdA = make_lazy_plan(true, false, 2, 12, 16);
-constexpr LazyPlan kPlanFwdD = make_lazy_plan(true, true, 2, 8, 4);
-constexpr LazyPlan kPlanInvD = make_lazy_plan(false, true, 2, 16, 16);
-constexpr LazyPlan kPlanInvA = make_lazy_plan(false, false, 2, 16, 2);
+// pointwise Montgomery step, outputs < 32q into the Shoup twiddle) and
+// stage A' (negacyclic GS, inputs [0, 2q), outputs [0, 2q)).  The
+// thresholds are the ones that need the fewest reductions.
+constexpr LazyPlan kPlanFwdA = make_lazy_plan(true, false, 2, 12, kLazyMax);
+constexpr LazyPlan kPlanFwdD = make_lazy_plan(true, true, 2, 8, 8);
+constexpr LazyPlan kPlanInvD = make_lazy_plan(false, true, 2, kLazyMax, kLazyMax);
+constexpr LazyPlan kPlanInvA = make_lazy_plan(false, false, 2, kLazyMax, 2);
 static_assert(kPlanFwdA.ok && kPlanFwdD.ok && kPlanInvD.ok && kPlanInvA.ok, "lazy plan");
-static_assert(kPlanFwdA.reductions == 0 && kPlanFwdD.reductions == 65 &&
-              kPlanInvD.reductions == 14 && kPlanInvA.reductions == 36, "lazy plan size");
+static_assert(kPlanFwdA.reductions == 0 && kPlanFwdD.reductions == 33 &&
+              kPlanInvD.reductions == 4 && kPlanInvA.reductions == 32, "lazy plan size");
 
 __device__ __forceinline__ uint32_t lazy_reduce_n(uint32_t x, const uint8_t (&ks)[4], int n,
                                                   const Prime &pr)
@@ -206,8 +215,7 @@ __device__ __forceinline__ uint32_t lazy_reduce_n(uint32_t x, const uint8_t (&ks
 template <bool CYC>
 __device__ __forceinline__ void ct32(uint32_t (&x)[32], const Prime &pr)
 {
-    constexpr LazyPlan PL = CYC ? make_lazy_plan(true, true, 2, 8, 4)
-                                : make_lazy_plan(true, false, 2, 12, 16);
+    constexpr LazyPlan PL = CYC ? kPlanFwdD : kPlanFwdA;
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int m = 1 << s, ln = 16 >> s;
@@ -238,8 +246,7 @@ __device__ __forceinline__ void ct32(uint32_t (&x)[32], const Prime &pr)
 template <bool CYC>
 __device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 {
-    constexpr LazyPlan PL = CYC ? make_lazy_plan(false, true, 2, 16, 16)
-                                : make_lazy_plan(false, false, 2, 16, 2);
+    constexpr LazyPlan PL = CYC ? kPlanInvD : kPlanInvA;
 #pragma unroll
     for (int s = 4; s >= 0; --s) {
         const int m = 1 << s, ln = 16 >> s;
@@ -268,7 +275,7 @@ __device__ __forceinline__ void gs32(uint32_t (&x)[32], const Prime &pr)
 // Forward negacyclic NTT of one polynomial held by one warp.
 // In : lane l, register r holds coefficient l + 32 r, value in [0, 2q).
 // Out: lane l, register r holds the evaluation at psi^(2 (l + 32 brv5(r)) + 1),
-//      value in [0, 4q).  sbuf: kSlot words of this warp's shared memory.
+//      value in [0, 8q).  sbuf: kSlot words of this warp's shared memory.
 __device__ __forceinline__ void fwd_ntt(uint32_t (&x)[32], uint32_t *sbuf, int lane,
                                         const uint2 *__restrict__ twb, const Prime &pr)
 {
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(128) k_bk_to_ntt(const int32_t *__restrict__ b
     uint32_t *dst = out + ((((i * 2 + p) * 2 + qsel) * 32) * 32 + lane) * 4 + r;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        uint32_t v = x[k] % q;                         // [0, 4q) -> [0, q)
+        uint32_t v = x[k] % q;                         // [0, 8q) -> [0, q)
         v = csub(mul_shoup(v, sc, scp, q), q);        // * 2^32 N^-1, in [0, q)
         dst[k * 32 * 4] = v;
     }
@@ -480,7 +487,8 @@ __device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4,
 // added into the accumulator.  Warp (p, h) does registers 16h .. 16h + 15.
 // Garner: u = (r1 - r0) q0^-1 mod q1, v = r0 + q0 u in [0, q0 q1).  The
 // exact coefficient S satisfies |S| <= 4 N 2^9 2^31 = 2^52, so for S >= 0
-// u = floor(S / q0) < 2^25, and for S < 0 (v = S + q0 q1) u > q1 - 2^25:
+// u = floor(S / q0) <= 2^52 / q0 < 2^25 + 2^9, and for S < 0
+// (v = S + q0 q1) u >= q1 - 2^25 - 2^9; both primes exceed 2^26 + 2^25, so
 // the centring decision (v >= q0 q1 / 2) is exactly u > (q1 - 1) / 2.
 // The calling warp lifts registers r0 .. r0 + NR - 1 of polynomial p.
 template <int NR>

@@ -27,13 +27,16 @@ constexpr uint32_t kMu = 1u << 29;       // 1/8
 // 1/2 Bg per level plus the rounding half of the last level.
 constexpr uint32_t kDecompOffset = (1u << 31) + (1u << 21) + (1u << 11);
 
-// Two NTT primes below 2^28 with 2048 | q - 1.  Their product P ~ 2^56
+// Two NTT primes below 2^27 with 2048 | q - 1.  Their product P ~ 2^54
 // exceeds twice the largest magnitude of an exact external-product
 // coefficient, 4 * N * 2^9 * 2^31 = 2^52, so the centred CRT lift is the
-// exact integer.  q < 2^28 keeps every lazy value below 2^32 and the 4-term
-// pointwise sum of [0,4q) x [0,q) products below q * 2^32.
-constexpr uint32_t kQ0 = 268369921u;     // 0x0FFF0001
-constexpr uint32_t kQ1 = 268367873u;     // 0x0FFEF801
+// exact integer.  q < 2^27 keeps every lazy value below 32 q < 2^32 and the
+// 4-term pointwise sum of [0,8q) x [0,q) products below q * 2^32.
+constexpr uint32_t kQ0 = 134215681u;     // 0x07FFF801
+constexpr uint32_t kQ1 = 134203393u;     // 0x07FFC801
+static_assert(32ull * kQ0 < (1ull << 32) && 32ull * kQ1 < (1ull << 32), "lazy bound");
+static_assert((kQ0 - 1) % 2048 == 0 && (kQ1 - 1) % 2048 == 0, "2N-th roots of unity");
+static_assert((unsigned __int128)kQ0 * kQ1 > ((unsigned __int128)1 << 53), "centred CRT lift");
 
 // Status word bits (device-side errors).
 constexpr uint32_t kErrGather = 1u;
