@@ -121,8 +121,14 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
         int8_t br[8] = {0}, ks[8] = {0};
         for (int b = 0; b < 8 && e == cudaSuccess; ++b) {
             const long W = widths[b];
+            // candidates from the finest launch granularity up: a later one
+            // is kept only if it is at least 2 % faster, because the timing
+            // is taken at the bucket's widest level (whole waves), where
+            // 1, 2 and 4 bootstraps per CTA tie, while the bucket's narrower
+            // levels end in part-filled waves that the finer shapes spread
+            // over more SMs
             float best = 1e30f;
-            for (int B : {1, 2, 4, kBrSplit, kBrPair}) {
+            for (int B : {kBrSplit, kBrPair, 1, 2, 4}) {
                 // the latency shapes hold one bootstrap per SM (or SM pair):
                 // only candidates while a level fits in about one wave of them
                 if ((B == kBrSplit || B == kBrPair) && W > 2L * ctx->num_sms)
@@ -142,7 +148,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
                     if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
                         tot += ms;   // first run is a warm-up
                 }
-                if (e == cudaSuccess && tot < best) {
+                if (e == cudaSuccess && (br[b] == 0 || tot < 0.98f * best)) {
                     best = tot;
                     br[b] = (int8_t)B;
                 }
