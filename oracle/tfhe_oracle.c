@@ -21,7 +21,10 @@
  *   - Boolean circuits: ripple-carry adder (Eq. "addres", Eq. "addcarry",
  *     sections III-A and V-B-1), naive shift-and-add multiplication (section
  *     III-B-1) and the matrix-vector product of section IV-D with the
- *     tree-based accumulation of section V-B-2.
+ *     tree-based accumulation of section V-B-2; and the variants: the
+ *     number-wise adder of section V-B-1, majority-carry adders, tree
+ *     multiplication, full products naive and by Karatsuba (section III-B),
+ *     and the low-depth parallel-prefix adder and Dadda multiplier.
  *
  * Every polynomial product here is the schoolbook definition of a product in
  * Z[X]/(X^N+1) evaluated with uint32 wraparound, i.e. exactly mod 2^32.
