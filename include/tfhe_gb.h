@@ -195,7 +195,7 @@ int tfhe_matvec(tfhe_ctx *ctx, int width, int rows, int cols, const int32_t *M,
  * batch) is compiled once and cached; its level sequence is replayed as a
  * CUDA graph. */
 typedef enum {
-    TFHE_CIRCUIT_GATE = 0,     /* one 2-input gate, opcode in `width`             */
+    TFHE_CIRCUIT_GATE = 0,     /* one 2-input gate, opcode in `width` (not MAJ)   */
     TFHE_CIRCUIT_ADD = 1,      /* tfhe_add_n: ripple carry, 5w - 6 gates, depth 2w-2 */
     TFHE_CIRCUIT_MUL = 2,      /* tfhe_mul_n: sequential shift-and-add           */
     TFHE_CIRCUIT_MATVEC = 3,   /* tfhe_matvec (rows x cols)                      */
@@ -255,6 +255,16 @@ int tfhe_schedule_info(const tfhe_job *jobs, size_t njobs, int policy, int64_t t
 /* Bootstrapped-gate count and depth (levels) of one instance of a circuit;
  * needs no context and no GPU. */
 int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, int32_t *depth);
+
+/* Host-only: evaluate one instance of a circuit on plaintext bits, gate by
+ * gate through the same netlist the GPU schedules run (no counterpart in
+ * the paper; it lets a CPU check the circuit definitions).  in: n_in bits
+ * (0/1), the input wires in the order of the circuit's inputs (A bits then
+ * B bits, least significant first; MATVEC: M[r][c] bits then v[c] bits);
+ * out: n_out bits in output order.  TFHE_EINVAL if the circuit is
+ * unsupported or the counts do not match.  Needs no context and no GPU. */
+int tfhe_circuit_eval_plain(int kind, int width, int rows, int cols, const uint8_t *in,
+                            size_t n_in, uint8_t *out, size_t n_out);
 
 /* Context options. */
 typedef enum {

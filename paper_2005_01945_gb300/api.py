@@ -73,6 +73,10 @@ EXPORTS = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "tfhe_circuit_info": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int64),
                                                                ctypes.POINTER(ctypes.c_int32)]),
+    "tfhe_circuit_eval_plain": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_void_p,
+                                                                     ctypes.c_size_t,
+                                                                     ctypes.c_void_p,
+                                                                     ctypes.c_size_t]),
     "tfhe_ctx_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "tfhe_ctx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]),
     "tfhe_ctx_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
@@ -380,6 +384,16 @@ def circuit_info(kind, width, rows=0, cols=0):
     g, d = ctypes.c_int64(0), ctypes.c_int32(0)
     _check(lib().tfhe_circuit_info(kind, width, rows, cols, ctypes.byref(g), ctypes.byref(d)))
     return int(g.value), int(d.value)
+
+
+def circuit_eval_plain(kind, width, in_bits, n_out, rows=0, cols=0) -> np.ndarray:
+    """Host-only: the circuit's netlist evaluated on plaintext bits (uint8
+    0/1 input wires in circuit order) -> n_out output bits."""
+    inp = np.ascontiguousarray(np.asarray(in_bits, dtype=np.uint8))
+    out = np.zeros(n_out, dtype=np.uint8)
+    _check(lib().tfhe_circuit_eval_plain(kind, width, rows, cols, _ptr(inp), inp.size,
+                                         _ptr(out), n_out))
+    return out
 
 
 # ------------------------------------------------------------- client side

@@ -425,8 +425,8 @@ static std::vector<int> range_wires(int start, int count)
 bool build_netlist(int kind, int w, int rows, int cols, Netlist &nl)
 {
     switch (kind) {
-    case TFHE_CIRCUIT_GATE:
-        if (w < 0 || w > TFHE_XNOR)
+    case TFHE_CIRCUIT_GATE:   // any two-input opcode (not the 3-input MAJ)
+        if (w < 0 || w > TFHE_ORYN || w == TFHE_MAJ)
             return false;
         nl.n_in = 2;
         nl.out = {nl.gate(w, 0, 1)};
@@ -1178,6 +1178,42 @@ int tfhe_circuit_info(int kind, int width, int rows, int cols, int64_t *gates, i
         *gates = (int64_t)nl.op.size();
     if (depth)
         *depth = nl.depth;
+    return TFHE_OK;
+}
+
+int tfhe_circuit_eval_plain(int kind, int width, int rows, int cols, const uint8_t *in,
+                            size_t n_in, uint8_t *out, size_t n_out)
+{
+    const std::shared_ptr<const Netlist> keep = get_netlist(kind, width, rows, cols);
+    if (!keep)
+        return TFHE_EINVAL;
+    const Netlist &nl = *keep;
+    if (!in || !out || n_in != (size_t)nl.n_in || n_out != nl.out.size())
+        return TFHE_EINVAL;
+    std::vector<uint8_t> v(nl.wires());
+    for (int i = 0; i < nl.n_in; ++i)
+        v[i] = in[i] & 1u;
+    for (size_t g = 0; g < nl.op.size(); ++g) {
+        const int a = v[nl.a[g]], b = v[nl.b[g]], c = nl.c[g] >= 0 ? v[nl.c[g]] : 0;
+        int r;
+        switch (nl.op[g]) {
+        case TFHE_NAND:  r = !(a & b); break;
+        case TFHE_AND:   r = a & b; break;
+        case TFHE_OR:    r = a | b; break;
+        case TFHE_XOR:   r = a ^ b; break;
+        case TFHE_NOR:   r = !(a | b); break;
+        case TFHE_XNOR:  r = !(a ^ b); break;
+        case TFHE_MAJ:   r = (a + b + c) >= 2; break;
+        case TFHE_ANDNY: r = !a & b; break;
+        case TFHE_ANDYN: r = a & !b; break;
+        case TFHE_ORNY:  r = !a | b; break;
+        case TFHE_ORYN:  r = a | !b; break;
+        default:         return TFHE_EINVAL;
+        }
+        v[nl.n_in + g] = (uint8_t)r;
+    }
+    for (size_t o = 0; o < nl.out.size(); ++o)
+        out[o] = v[nl.out[o]];
     return TFHE_OK;
 }
 
