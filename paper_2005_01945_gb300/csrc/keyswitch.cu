@@ -470,7 +470,9 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
 // Launch
 // ---------------------------------------------------------------------
 
-static int ks_forced_chunks = 0;   // set while the autotuner measures
+// Set while the autotuner measures, for the launches of its own thread
+// only (other threads' contexts keep their choices).
+static thread_local int ks_forced_chunks = 0;
 
 // Launch choice: kKsTiled selects the tiled kernel, 1..32 the j-chunks of
 // k_keyswitch.  A forced choice (autotuner, TFHE_OPT_KS_KERNEL) wins, then
