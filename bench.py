@@ -40,7 +40,7 @@ BATCH, WIDTH = 256, 32
 GATES_PER_ADD = 5 * WIDTH - 6
 
 # Algorithmic 32-bit integer operations of one CMux step of the NTT-based
-# external product (derivation in DESIGN.md, "Roofline"): 12 transforms of
+# external product: 12 transforms of
 # 5120 radix-2 butterflies at 7 ops, 12 x 1024 twiddle products at 3 ops,
 # 2 x 2 x 1024 pointwise 4-term products at 12 ops, 4 x 1024 digit
 # extractions at 8 ops, 2 x 1024 CRT lifts + accumulates at 12 ops.
