@@ -51,7 +51,7 @@ typedef struct tfhe_ctx tfhe_ctx; /* opaque, owned by the library */
 /* Parameter set (section II-A names LWE dimension and key size; the values
  * are those of TFHE's gate bootstrapping): LWE dimension n, TLWE ring degree
  * N with k = 1, gadget base 2^bg_bit with l levels, key-switch base
- * 2^ks_basebit with ks_t levels.  This build supports n <= 511, N = 1024,
+ * 2^ks_basebit with ks_t levels.  The library supports n <= 511, N = 1024,
  * k = 1, bg_bit = 10, l = 2, ks_t = 8, ks_basebit = 2; anything else is
  * rejected with TFHE_EINVAL. */
 typedef struct {
