@@ -153,18 +153,25 @@ def _ptr(x):
     if x is None:
         return None
     if isinstance(x, np.ndarray):
-        assert x.flags["C_CONTIGUOUS"]
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
         return ctypes.c_void_p(x.ctypes.data)
-    assert x.is_contiguous(), "tensors passed to the library must be contiguous"
+    if not x.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
     return ctypes.c_void_p(x.data_ptr())
 
 
 def _dev(x, dtype=None):
+    """Device pointer of a contiguous CUDA tensor; anything else is refused
+    (the library computes on the GPU only)."""
     import torch
-    assert isinstance(x, torch.Tensor) and x.is_cuda, "expected a CUDA tensor"
-    if dtype is not None:
-        assert x.dtype == dtype, f"expected {dtype}, got {x.dtype}"
-    assert x.is_contiguous()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"expected a CUDA tensor, got {type(x).__name__}"
+                        + (f" on {x.device}" if isinstance(x, torch.Tensor) else ""))
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
     return ctypes.c_void_p(x.data_ptr())
 
 
