@@ -175,6 +175,35 @@ def _dev(x, dtype=None):
     return ctypes.c_void_p(x.data_ptr())
 
 
+def _need(x, rows, name, stride=LWE_STRIDE):
+    """Refuse a buffer that holds fewer than rows x stride words: the library
+    trusts the sizes it is given, so a short buffer would be overrun on the
+    device."""
+    if x is not None and x.numel() < rows * stride:
+        raise TFHEError(-1, f"{name} holds {x.numel()} words, needs {rows} x {stride}")
+
+
+def job_rows(kind, width, rows=0, cols=0):
+    """Ciphertext rows (in0, in1, out) of one instance of a circuit job:
+    GATE 1, 1, 1; MATVEC rows*cols*w, cols*w, rows*w; full products w, w,
+    2w; every other circuit w, w, w."""
+    if kind == GATE:
+        return 1, 1, 1
+    if kind == MATVEC:
+        return rows * cols * width, cols * width, rows * width
+    if kind in (MUL_FULL, MUL_KARATSUBA):
+        return width, width, 2 * width
+    return width, width, width
+
+
+def _need_job(batch, kind, width, rows, cols, in0, in1, out):
+    r0, r1, ro = job_rows(kind, width, rows, cols)
+    if batch > 0 and min(r0, r1, ro) > 0:
+        _need(in0, batch * r0, "in0")
+        _need(in1, batch * r1, "in1")
+        _need(out, batch * ro, "out")
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -240,6 +269,8 @@ class Context:
     def bootstrap_gates(self, ops, a, b, out, stream=None):
         import torch
         count = ops.numel()
+        for t, name in ((a, "a"), (b, "b"), (out, "out")):
+            _need(t, count, name)
         self._c(lib().tfhe_bootstrap_gates(self._h, _dev(ops, torch.uint8), _dev(a, torch.int32),
                                            _dev(b, torch.int32), _dev(out, torch.int32), count,
                                            _stream(stream)))
@@ -250,6 +281,8 @@ class Context:
         overlap on the GPU race)."""
         import torch
         count = ops.numel()
+        for t, name in ((a, "a"), (b, "b"), (out, "out")):
+            _need(t, count, name)
         self._c(lib().tfhe_bootstrap_gates_noalloc(
             self._h, _dev(ops, torch.uint8), _dev(a, torch.int32), _dev(b, torch.int32),
             _dev(out, torch.int32), count, _stream(stream)))
@@ -257,12 +290,18 @@ class Context:
     def bootstrap(self, x, out, mu=MU, stream=None):
         import torch
         count = x.shape[0]
+        _need(x, count, "x")
+        _need(out, count, "out")
         self._c(lib().tfhe_bootstrap(self._h, _dev(x, torch.int32), _dev(out, torch.int32), count,
                                      mu, _stream(stream)))
 
     def blind_rotate_extract(self, ops, a, b, big, stream=None):
         import torch
         count = a.shape[0]
+        _need(a, count, "a")
+        _need(b, count, "b")
+        _need(ops, count, "ops", 1)
+        _need(big, count, "big", BIG_STRIDE)
         self._c(lib().tfhe_blind_rotate_extract(
             self._h, None if ops is None else _dev(ops, torch.uint8), _dev(a, torch.int32),
             None if b is None else _dev(b, torch.int32), _dev(big, torch.int32), count,
@@ -270,24 +309,29 @@ class Context:
 
     def keyswitch(self, big, out, stream=None):
         import torch
+        _need(big, big.shape[0], "big", BIG_STRIDE)
+        _need(out, big.shape[0], "out")
         self._c(lib().tfhe_keyswitch(self._h, _dev(big, torch.int32), _dev(out, torch.int32),
                                      big.shape[0], _stream(stream)))
 
     def add_n(self, width, A, B, R, stream=None):
         import torch
         batch = A.shape[0]
+        _need_job(batch, ADD, width, 0, 0, A, B, R)
         self._c(lib().tfhe_add_n(self._h, width, _dev(A, torch.int32), _dev(B, torch.int32),
                                  _dev(R, torch.int32), batch, _stream(stream)))
 
     def mul_n(self, width, A, B, R, stream=None):
         import torch
         batch = A.shape[0]
+        _need_job(batch, MUL, width, 0, 0, A, B, R)
         self._c(lib().tfhe_mul_n(self._h, width, _dev(A, torch.int32), _dev(B, torch.int32),
                                  _dev(R, torch.int32), batch, _stream(stream)))
 
     def matvec(self, width, M, v, y, stream=None):
         import torch
         rows, cols = M.shape[0], M.shape[1]
+        _need_job(1, MATVEC, width, rows, cols, M, v, y)
         self._c(lib().tfhe_matvec(self._h, width, rows, cols, _dev(M, torch.int32),
                                   _dev(v, torch.int32), _dev(y, torch.int32), _stream(stream)))
 
@@ -297,6 +341,8 @@ class Context:
         (device tensors).  All jobs share one level schedule."""
         arr = (CJob * len(jobs))()
         for k, j in enumerate(jobs):
+            _need_job(j["batch"], j["kind"], j["width"], j.get("rows", 0), j.get("cols", 0),
+                      j["in0"], j["in1"], j["out"])
             arr[k] = CJob(j["kind"], j["width"], j.get("rows", 0), j.get("cols", 0), j["batch"],
                           _dev(j["in0"]).value, _dev(j["in1"]).value, _dev(j["out"]).value)
         self._c(lib().tfhe_run_jobs(self._h, arr, len(jobs), _stream(stream)))
@@ -336,6 +382,7 @@ class Context:
         self._c(lib().tfhe_serve_start(self._h, int(hbm_budget_bytes), int(max_batch_gates)))
 
     def serve_submit(self, kind, width, in0, in1, out, rows=0, cols=0) -> int:
+        _need_job(1, kind, width, rows, cols, in0, in1, out)
         req = CRequest(kind, width, rows, cols, _dev(in0).value, _dev(in1).value,
                        _dev(out).value)
         rid = ctypes.c_uint64(0)
