@@ -108,3 +108,22 @@ def test_rejects_bad_counts_and_kinds(api):
         api.circuit_eval_plain(api.ADD, 4, [0] * 8, 5)
     with pytest.raises(api.TFHEError):
         api.circuit_eval_plain(99, 4, [0] * 8, 4)
+
+
+def test_documented_gate_counts_and_depths(api):
+    """The counts and depths the header states, at every width 1..64:
+    ripple adder 5w - 6 gates in 2w - 2 levels (w = 1: one XOR), majority
+    adder 3w - 2 gates in w levels, number-wise adder w^2 gates in w levels,
+    prefix adder ceil(log2(w - 1)) + 2 levels (w >= 3); width 65 is
+    refused."""
+    import math
+    for w in range(1, 65):
+        assert api.circuit_info(api.ADD, w) == ((5 * w - 6, 2 * w - 2) if w > 1 else (1, 1))
+        if w > 1:
+            assert api.circuit_info(api.ADD_MAJ, w) == (3 * w - 2, w)
+        assert api.circuit_info(api.ADD_NW, w) == (w * w, w)
+        if w >= 3:
+            assert api.circuit_info(api.ADD_PREFIX, w)[1] == math.ceil(math.log2(w - 1)) + 2
+    for kind in (api.ADD, api.MUL, api.ADD_PREFIX, api.MUL_DADDA, api.MUL_FULL):
+        with pytest.raises(api.TFHEError):
+            api.circuit_info(kind, 65)
