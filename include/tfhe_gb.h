@@ -160,12 +160,16 @@ int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count
  * TFHE_NOALLOC_MAX_GATES rows (2,162,688 bytes) in the library's device
  * image, which every GPU that loads the library holds until the process
  * exits.  count > TFHE_NOALLOC_MAX_GATES is rejected with TFHE_EINVAL
- * (split the batch).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make that first call before
- * any stream capture.  All calls on a device share the one array: calls
- * that overlap on the GPU (other streams, other contexts on the same
- * device) race and must be serialised by the caller.  Nothing in the array
- * needs clearing between calls. */
+ * (split the batch).  The first call on a device (and the first after a
+ * device reset, which reloads the library's device image) looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it for that
+ * CUDA context, so make that first call before any stream capture.  It
+ * launches the same kernels as tfhe_bootstrap_gates, including the
+ * context's key-switch kernel choice (TFHE_OPT_KS_KERNEL, autotuner).  All
+ * calls on a device share the one array: calls that overlap on the GPU
+ * (other streams, other contexts on the same device) race and must be
+ * serialised by the caller.  Nothing in the array needs clearing between
+ * calls. */
 #define TFHE_NOALLOC_MAX_GATES 512
 int tfhe_bootstrap_gates_noalloc(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a,
                                  const int32_t *b, int32_t *out, size_t count, void *stream);
@@ -286,10 +290,11 @@ typedef enum {
                              /*    1, 2, 4, .. 32 = direct kernel with that j-split, */
                              /*    or 0 (default): autotuned, else by batch size    */
     TFHE_OPT_TEST_KS_STALL = 7 /* test hook for the timeout path, 0 (default) off:  */
-                             /*    1 makes every stage of the tiled key switch wait */
-                             /*    for 16 bytes that never arrive, so each bounded  */
-                             /*    wait runs out after a short budget; the call     */
-                             /*    then sets status bit 2 (timeout), its outputs    */
+                             /*    1 makes every stage of the tiled key switch also */
+                             /*    wait on an mbarrier that nothing completes, so   */
+                             /*    each bounded wait runs out after a short budget; */
+                             /*    the kernel then lets the copies it issued land,  */
+                             /*    the call sets status bit 2 (timeout), its outputs */
                              /*    are undefined, and the context stays usable     */
 } tfhe_option;
 

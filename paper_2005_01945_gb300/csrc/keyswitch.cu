@@ -42,8 +42,8 @@ struct KsArgs {
     int atomic;               // 1: add into pre-initialised rows
     uint32_t *status;
     long spin;                // tiled kernel: tries of one bounded mbarrier wait
-    uint32_t stall_tx;        // tiled kernel, test hook: extra bytes each stage expects
-                              // (non-zero: no stage completes, every wait runs out)
+    int stall;                // tiled kernel, test hook: every stage's wait also waits
+                              // on a barrier that nothing completes, so it runs out
 };
 
 __device__ __forceinline__ long ks_dest(const KsArgs &A, long g)
@@ -177,6 +177,7 @@ struct KtSmem {
     uint4 zero[kKtVecs];                             // 1 KB of zeros (digit pair 00)
     uint16_t w[kKtWin][kKtWStride];                  // rounded a'_j [j][gate] (18 KB)
     unsigned long long full[kKtStages];              // mbarriers: stage landed
+    unsigned long long never;                        // test hook: never completes
     int abort;                                       // a wait ran out: stop
     uint32_t abort_it;                               // ... at this stage
 };
@@ -290,7 +291,7 @@ __device__ __forceinline__ void kt_issue(const KsArgs &A, KtSmem &S, int slot, i
 {
     if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&S.full[slot], kKtStageBytes + A.stall_tx);
+        mbar_expect_tx(&S.full[slot], kKtStageBytes);
     }
     __syncwarp();
     if (lane < kKtRows) {
@@ -322,6 +323,7 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
     if (tid == 0) {
         for (int s = 0; s < kKtStages; ++s)
             mbar_init(&S.full[s], 1);
+        mbar_init(&S.never, 1);   // no thread ever arrives on it
         S.abort = 0;
         S.abort_it = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -363,7 +365,8 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
                 __syncthreads();
             }
             const int slot = it % kKtStages;
-            if (!S.abort && !mbar_wait_bounded(&S.full[slot], (it / kKtStages) & 1u, A.spin)) {
+            if (!S.abort && (!mbar_wait_bounded(&S.full[slot], (it / kKtStages) & 1u, A.spin) ||
+                             (A.stall && !mbar_wait_bounded(&S.never, 0u, A.spin)))) {
                 S.abort_it = it;   // the same value in every thread that gets here
                 S.abort = 1;
                 atomicOr(A.status, kErrTimeout);
@@ -460,7 +463,9 @@ __global__ void __launch_bounds__(32 * kKtWarps, 2) k_keyswitch_tiled(const KsAr
         __syncthreads();   // the ring is free for the next tile's copies
     }
     // after a timed-out wait: give the stages issued but never waited for a
-    // bounded time to land before the CTA's shared memory is released
+    // bounded time to land before the CTA's shared memory is released (their
+    // barriers count only the real copies' bytes, so under the test hook
+    // these waits end as soon as the copies have landed)
     if (warp == 0 && lane == 0 && S.abort)
         for (uint32_t p = S.abort_it; p < issued; ++p)
             (void)mbar_wait_bounded(&S.full[p % kKtStages], (p / kKtStages) & 1u, A.spin);
@@ -535,7 +540,7 @@ cudaError_t launch_keyswitch(const uint4 *ksk, const int32_t *big, int32_t *out,
     A.status = status;
     const bool stall = tiled && choice && choice->ks_stall;
     A.spin = stall ? kKtStallSpin : kKtSpin;
-    A.stall_tx = stall ? 16u : 0u;
+    A.stall = stall ? 1 : 0;
     if (A.atomic) {
         k_ks_init<<<(unsigned)count, 128, 0, stream>>>(A);
         cudaError_t e = cudaGetLastError();

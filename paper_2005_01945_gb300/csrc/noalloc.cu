@@ -28,26 +28,69 @@ constexpr long kNoAllocMaxGates = TFHE_NOALLOC_MAX_GATES;
 static __device__ __align__(256) int32_t g_noalloc_big[kNoAllocMaxGates * kBigStride];
 
 // In host code the name g_noalloc_big is only a host-side stand-in, not a
-// device address: the device address is looked up once per device, with
-// that device current, and cached here.
-constexpr int kNoAllocMaxDevices = 64;
-static int32_t *g_noalloc_dev_ptr[kNoAllocMaxDevices];
+// device address.  The device address is looked up with the device current
+// and cached per CUDA context: a device reset (or another context made
+// current) loads the library's device image anew, where the array may sit
+// elsewhere, so a cached address is used only for the context that gave it.
+// The context handle comes from the driver's cuCtxGetCurrent, reached
+// through the runtime's entry-point query (no link against the driver).
+constexpr int kNoAllocMaxSlots = 64;
+struct NoAllocSlot {
+    void *cu_ctx;
+    int32_t *ptr;
+};
+static NoAllocSlot g_noalloc_slots[kNoAllocMaxSlots];
+static int g_noalloc_nslots = 0;
 static std::mutex g_noalloc_mutex;
 
+typedef int (*cu_ctx_get_current_fn)(void **);
+
+static int current_cu_context(tfhe_ctx *ctx, void **cu_ctx)
+{
+    static cu_ctx_get_current_fn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return fail(ctx, TFHE_ECUDA, "tfhe_bootstrap_gates_noalloc: cuCtxGetCurrent "
+                        "unavailable (%s)", cudaGetErrorString(e));
+        fn = (cu_ctx_get_current_fn)f;
+    }
+    *cu_ctx = nullptr;
+    if (fn(cu_ctx) != 0 || !*cu_ctx)
+        return fail(ctx, TFHE_ECUDA, "tfhe_bootstrap_gates_noalloc: no current CUDA context");
+    return TFHE_OK;
+}
+
+// Set-up, once per device (per CUDA context on it), with that device
+// current: the caller holds a DeviceGuard for ctx->device.
 static int noalloc_scratch(tfhe_ctx *ctx, int32_t **ptr)
 {
-    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
-        return fail(ctx, TFHE_EINVAL, "tfhe_bootstrap_gates_noalloc: device %d out of range",
-                    ctx->device);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_dev_ptr[ctx->device]) {
-        int32_t *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_big);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_dev_ptr[ctx->device] = p;
-    }
-    *ptr = g_noalloc_dev_ptr[ctx->device];
+    // cudaSetDevice (the caller's DeviceGuard) has made the device's primary
+    // context current.
+    void *cu_ctx = nullptr;
+    int rc = current_cu_context(ctx, &cu_ctx);
+    if (rc != TFHE_OK)
+        return rc;
+    for (int i = 0; i < g_noalloc_nslots; i++)
+        if (g_noalloc_slots[i].cu_ctx == cu_ctx) {
+            *ptr = g_noalloc_slots[i].ptr;
+            return TFHE_OK;
+        }
+    int32_t *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_big);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+    // When the table is full, new entries overwrite the oldest from slot 0
+    // (an entry of a context that no longer exists is only a lookup that
+    // misses).
+    if (g_noalloc_nslots == kNoAllocMaxSlots)
+        g_noalloc_nslots = 0;
+    g_noalloc_slots[g_noalloc_nslots++] = {cu_ctx, p};
+    *ptr = p;
     return TFHE_OK;
 }
 
@@ -84,9 +127,9 @@ extern "C" int tfhe_bootstrap_gates_noalloc(tfhe_ctx *ctx, const uint8_t *ops, c
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "blind rotation launch");
     e = launch_keyswitch(ctx->keys.ksk, big, out, nullptr, n, n, ctx->prm.n, ctx->num_sms,
-                         ctx->status, st);
+                         ctx->status, st, &ctx->keys);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "key switch launch");
-    ctx->launches += 1 + keyswitch_kernels(n, ctx->num_sms);
+    ctx->launches += 1 + keyswitch_kernels(n, ctx->num_sms, &ctx->keys);
     return TFHE_OK;
 }

@@ -188,9 +188,9 @@ def test_keyswitch_beyond_one_grid_of_tiles(env):
 
 def test_keyswitch_wait_timeout_is_reported_and_recoverable(env):
     """Failure detection without a GPU fault: with the stall test hook every
-    stage of the tiled key switch waits on an mbarrier for 16 bytes that no
-    copy delivers.  Each bounded wait runs out, the kernel records the
-    timeout (status bit 2) and returns; the next call on the same context,
+    stage of the tiled key switch also waits on an mbarrier that nothing
+    completes.  Each bounded wait runs out, the kernel records the timeout
+    (status bit 2), lets the copies it issued land, and returns; the next call on the same context,
     hook off, is bit-exact against the oracle."""
     torch, api, orc, p = env.torch, env.api, env.orc, env.p
     count = 70

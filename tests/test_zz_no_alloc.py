@@ -4,9 +4,10 @@ exactly the same ciphertexts as tfhe_bootstrap_gates.
 It exists for callers that cannot let the library allocate device memory
 during a call (pre-reserved memory budgets, allocation-free serving loops).
 Its scratch is a fixed array shared by all calls on the device, so the
-test runs it twice in a row on different inputs (the second call must not
-depend on what the first left behind) and checks an oversize batch is
-refused.  The file sorts last so a stop-at-first-failure run has already
+test runs it several times in a row on different inputs, the larger call
+first (a later call must not depend on what an earlier one left behind),
+once on a side stream and once with another key-switch kernel chosen, and
+checks that an oversize batch is refused.  The file sorts last so a stop-at-first-failure run has already
 run every other test."""
 import numpy as np
 import pytest
@@ -43,17 +44,60 @@ def _batch(api, p, kd, count, seed):
     return ops, a, b
 
 
-def test_noalloc_matches_regular_entry_point_twice(env):
-    torch, api, p, kd, ctx = env
-    for call, (count, seed) in enumerate([(300, 1), (api.NOALLOC_MAX_GATES, 2)]):
-        ops, a, b = _batch(api, p, kd, count, seed)
-        ref = torch.empty((count, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
-        got = torch.full((count, api.LWE_STRIDE), -1, dtype=torch.int32, device="cuda")
-        ctx.bootstrap_gates(ops, a, b, ref)
+def _compare(torch, api, ctx, ops, a, b, stream=None):
+    count = ops.numel()
+    ref = torch.empty((count, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+    got = torch.full((count, api.LWE_STRIDE), -1, dtype=torch.int32, device="cuda")
+    ctx.bootstrap_gates(ops, a, b, ref)
+    torch.cuda.synchronize()
+    before = ctx.launches()
+    if stream is None:
         ctx.bootstrap_gates_noalloc(ops, a, b, got)
-        torch.cuda.synchronize()
-        assert torch.equal(got, ref), f"call {call}: outputs differ"
+    else:
+        with torch.cuda.stream(stream):
+            ctx.bootstrap_gates_noalloc(ops, a, b, got, stream=stream)
+    torch.cuda.synchronize()
+    return torch.equal(got, ref), ctx.launches() - before
+
+
+def test_noalloc_matches_regular_entry_point_in_a_row(env):
+    """A full-size call, then smaller ones: the smaller calls read rows of
+    the shared array that the larger call left behind, so they show that
+    nothing in it needs clearing.  The last call runs on a side stream."""
+    torch, api, p, kd, ctx = env
+    side = torch.cuda.Stream()
+    plan = [(api.NOALLOC_MAX_GATES, 2, None), (300, 1, None), (37, 5, side)]
+    for call, (count, seed, stream) in enumerate(plan):
+        ops, a, b = _batch(api, p, kd, count, seed)
+        same, _ = _compare(torch, api, ctx, ops, a, b, stream)
+        assert same, f"call {call} ({count} gates): outputs differ"
         assert ctx.status() == 0
+
+
+def test_noalloc_follows_the_key_switch_choice(env):
+    """With the direct key-switch kernel forced (TFHE_OPT_KS_KERNEL = 1: one
+    launch, where the tiled kernel takes two at this width), the
+    allocation-free call launches what tfhe_bootstrap_gates launches and
+    gives the same ciphertexts."""
+    torch, api, p, kd, ctx = env
+    ops, a, b = _batch(api, p, kd, 200, 7)
+    counts = {}
+    for choice in (1, api.KS_TILED):
+        ctx.set_option(api.OPT_KS_KERNEL, choice)
+        try:
+            torch.cuda.synchronize()
+            before = ctx.launches()
+            ref = torch.empty((200, api.LWE_STRIDE), dtype=torch.int32, device="cuda")
+            ctx.bootstrap_gates(ops, a, b, ref)
+            regular = ctx.launches() - before
+            same, noalloc = _compare(torch, api, ctx, ops, a, b)
+        finally:
+            ctx.set_option(api.OPT_KS_KERNEL, 0)
+        assert same, f"key-switch choice {choice}: outputs differ"
+        assert noalloc == regular, f"key-switch choice {choice}: {noalloc} vs {regular} launches"
+        counts[choice] = noalloc
+    assert counts[1] < counts[api.KS_TILED]
+    assert ctx.status() == 0
 
 
 def test_noalloc_rejects_oversize_batch(env):
