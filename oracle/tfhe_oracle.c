@@ -30,6 +30,11 @@
  * Z[X]/(X^N+1) evaluated with uint32 wraparound, i.e. exactly mod 2^32.
  * No randomness is drawn here: key bits, masks and noise are inputs.
  *
+ * Threads (OpenMP) only run independent work side by side: independent
+ * gates of a batch, and the gates of circuits as tasks ordered by the rows
+ * they read and write, so every result equals that of a one-by-one
+ * evaluation (see "Order of evaluation" below).
+ *
  * Parity of the noise statistics against a closed form is pinned in the
  * tests (measured variance vs. derived variance); every other function is
  * pinned against an independent computation (Karatsuba products, library
@@ -464,16 +469,126 @@ void orc_keyswitch_many(const orc_params *P, const uint32_t *ksk, int64_t count,
 /* Boolean circuits over encrypted integers (bit 0 = least significant) */
 /* ------------------------------------------------------------------ */
 
+/* Ciphertext rows of one evaluation (gate outputs and temporaries, n + 1
+ * words each).  A row is freed only when the whole evaluation -- every gate
+ * task that may read or write it -- has finished. */
+typedef struct {
+    uint32_t **buf;
+    int64_t n, cap, words;
+} orc_arena;
+
+/* `rows` consecutive rows in one block. */
+static uint32_t *arena_rows(orc_arena *A, int64_t rows)
+{
+    if (A->n == A->cap) {
+        A->cap = A->cap ? 2 * A->cap : 64;
+        A->buf = realloc(A->buf, sizeof(uint32_t *) * A->cap);
+    }
+    return A->buf[A->n++] = malloc(sizeof(uint32_t) * A->words * rows);
+}
+
+static uint32_t *arena_new(orc_arena *A)
+{
+    return arena_rows(A, 1);
+}
+
+static void arena_free(orc_arena *A)
+{
+    for (int64_t i = 0; i < A->n; i++)
+        free(A->buf[i]);
+    free(A->buf);
+}
+
 typedef struct {
     const orc_params *P;
     const uint32_t *bk, *ksk;
     int64_t gates;      /* bootstraps performed, for accounting */
+    orc_arena A;        /* every row the circuit allocates */
 } orc_ev;
 
+/* Order of evaluation.  Each gate (and each copy of a row) is an OpenMP task
+ * that names the rows it reads in depend(in) and the row it writes in
+ * depend(out), each row by its first word; rows never overlap partially.
+ * OpenMP then runs a task only after every earlier-created task that writes
+ * a row it reads, or reads or writes the row it writes, so the result is
+ * that of evaluating the gates one by one in the order the circuit code
+ * creates them (each ciphertext is a deterministic function of its gate's
+ * inputs), while independent gates of a circuit run on different threads.
+ * Without OpenMP the pragmas are ignored and the gates run in that order.
+ * The circuit functions below only build the task graph; the batched entry
+ * points at the end run it. */
 static void ev_gate(orc_ev *E, int32_t op, const uint32_t *a, const uint32_t *b, uint32_t *out)
 {
-    orc_gate(E->P, E->bk, E->ksk, op, a, b, out);
+    const orc_params *P = E->P;
+    const uint32_t *bk = E->bk, *ksk = E->ksk;
+#pragma omp task default(none) firstprivate(P, bk, ksk, op, a, b, out) \
+    depend(in : a[0], b[0]) depend(out : out[0])
+    orc_gate(P, bk, ksk, op, a, b, out);
     E->gates++;
+}
+
+static void ev_gate3(orc_ev *E, int32_t op, const uint32_t *a, const uint32_t *b,
+                     const uint32_t *c, uint32_t *out)
+{
+    const orc_params *P = E->P;
+    const uint32_t *bk = E->bk, *ksk = E->ksk;
+#pragma omp task default(none) firstprivate(P, bk, ksk, op, a, b, c, out) \
+    depend(in : a[0], b[0], c[0]) depend(out : out[0])
+    orc_gate3(P, bk, ksk, op, a, b, c, out);
+    E->gates++;
+}
+
+/* Row out = row in. */
+static void ev_copy(orc_ev *E, const uint32_t *in, uint32_t *out)
+{
+    const size_t bytes = sizeof(uint32_t) * (size_t)(E->P->n + 1);
+#pragma omp task default(none) firstprivate(bytes, in, out) depend(in : in[0]) depend(out : out[0])
+    memcpy(out, in, bytes);
+}
+
+/* Row out = the trivial sample (0, ..., 0, -1/8) of a constant-0 bit. */
+static void ev_const0(orc_ev *E, uint32_t *out)
+{
+    const int32_t n = E->P->n;
+#pragma omp task default(none) firstprivate(n, out) depend(out : out[0])
+    {
+        memset(out, 0, sizeof(uint32_t) * (size_t)(n + 1));
+        out[n] = (uint32_t)0 - ORC_MU;
+    }
+}
+
+static int32_t ev_threads(int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#endif
+    return nthreads > 0 ? nthreads : 1;
+}
+
+static orc_ev *ev_new_many(const orc_params *P, const uint32_t *bk, const uint32_t *ksk,
+                           int64_t count)
+{
+    orc_ev *E = calloc(count > 0 ? count : 1, sizeof(orc_ev));
+    for (int64_t i = 0; i < count; i++) {
+        E[i].P = P;
+        E[i].bk = bk;
+        E[i].ksk = ksk;
+        E[i].A.words = P->n + 1;
+    }
+    return E;
+}
+
+/* After the tasks have finished: total gates, rows freed. */
+static int64_t ev_free_many(orc_ev *E, int64_t count)
+{
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; i++) {
+        total += E[i].gates;
+        arena_free(&E[i].A);
+    }
+    free(E);
+    return total;
 }
 
 /* w-bit ripple-carry addition mod 2^w (sections III-A, V-B-1):
@@ -485,10 +600,8 @@ static void ev_gate(orc_ev *E, int32_t op, const uint32_t *a, const uint32_t *b,
 static void ev_add(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, uint32_t *R)
 {
     const int64_t W = E->P->n + 1;
-    uint32_t *x = malloc(sizeof(uint32_t) * W);
-    uint32_t *g = malloc(sizeof(uint32_t) * W);
-    uint32_t *t = malloc(sizeof(uint32_t) * W);
-    uint32_t *c = malloc(sizeof(uint32_t) * W);
+    uint32_t *x = arena_new(&E->A), *g = arena_new(&E->A);
+    uint32_t *t = arena_new(&E->A), *c = arena_new(&E->A);
     for (int32_t i = 0; i < w; i++) {
         const uint32_t *ai = A + i * W, *bi = B + i * W;
         uint32_t *ri = R + i * W;
@@ -506,7 +619,6 @@ static void ev_add(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, u
         ev_gate(E, ORC_AND, x, c, t);
         ev_gate(E, ORC_OR, g, t, c);
     }
-    free(x); free(g); free(t); free(c);
 }
 
 /* w x w -> w truncated naive multiplication (section III-B-1): partial
@@ -517,8 +629,8 @@ static void ev_add(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, u
 static void ev_mul(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, uint32_t *R)
 {
     const int64_t W = E->P->n + 1;
-    uint32_t *pp = malloc(sizeof(uint32_t) * W * w);
-    uint32_t *sum = malloc(sizeof(uint32_t) * W * w);
+    uint32_t *pp = arena_rows(&E->A, w);
+    uint32_t *sum = arena_rows(&E->A, w);
     for (int32_t j = 0; j < w; j++)                 /* partial product 0 */
         ev_gate(E, ORC_AND, A + j * W, B, R + j * W);
     for (int32_t i = 1; i < w; i++) {
@@ -526,9 +638,9 @@ static void ev_mul(orc_ev *E, int32_t w, const uint32_t *A, const uint32_t *B, u
         for (int32_t j = 0; j < m; j++)             /* a_j AND b_i, weight i+j */
             ev_gate(E, ORC_AND, A + j * W, B + i * W, pp + j * W);
         ev_add(E, m, R + i * W, pp, sum);
-        memcpy(R + i * W, sum, sizeof(uint32_t) * W * m);
+        for (int32_t j = 0; j < m; j++)
+            ev_copy(E, sum + j * W, R + (i + j) * W);
     }
-    free(pp); free(sum);
 }
 
 /* Matrix-vector product y_r = sum_c M[r][c] * v[c] mod 2^w (section IV-D:
@@ -541,8 +653,8 @@ static void ev_matvec_row(orc_ev *E, int32_t w, int32_t cols, const uint32_t *Mr
                           const uint32_t *v, uint32_t *Y)
 {
     const int64_t W = E->P->n + 1, num = W * w;
-    uint32_t *terms = malloc(sizeof(uint32_t) * num * cols);
-    uint32_t *next = malloc(sizeof(uint32_t) * num * cols);
+    uint32_t *terms = arena_rows(&E->A, (int64_t)cols * w);
+    uint32_t *next = arena_rows(&E->A, (int64_t)cols * w);
     for (int32_t c = 0; c < cols; c++)
         ev_mul(E, w, Mrow + c * num, v + c * num, terms + c * num);
     int32_t cnt = cols;
@@ -551,38 +663,20 @@ static void ev_matvec_row(orc_ev *E, int32_t w, int32_t cols, const uint32_t *Mr
         for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
             ev_add(E, w, terms + i * num, terms + (i + 1) * num, next + k * num);
         if (cnt & 1) {
-            memcpy(next + k * num, terms + (cnt - 1) * num, sizeof(uint32_t) * num);
+            for (int32_t j = 0; j < w; j++)
+                ev_copy(E, terms + (cnt - 1) * num + j * W, next + k * num + j * W);
             k++;
         }
-        memcpy(terms, next, sizeof(uint32_t) * num * k);
+        for (int64_t j = 0; j < (int64_t)k * w; j++)
+            ev_copy(E, next + j * W, terms + j * W);
         cnt = k;
     }
-    memcpy(Y, terms, sizeof(uint32_t) * num);
-    free(terms); free(next);
+    for (int32_t j = 0; j < w; j++)
+        ev_copy(E, terms + j * W, Y + j * W);
 }
 
-/* Wires that may be the constant 0 (NULL).  Every gate output gets a fresh
- * buffer from the arena, freed when the circuit is done. */
-typedef struct {
-    uint32_t **buf;
-    int64_t n, cap, words;
-} orc_arena;
-
-static uint32_t *arena_new(orc_arena *A)
-{
-    if (A->n == A->cap) {
-        A->cap = A->cap ? 2 * A->cap : 64;
-        A->buf = realloc(A->buf, sizeof(uint32_t *) * A->cap);
-    }
-    return A->buf[A->n++] = malloc(sizeof(uint32_t) * A->words);
-}
-
-static void arena_free(orc_arena *A)
-{
-    for (int64_t i = 0; i < A->n; i++)
-        free(A->buf[i]);
-    free(A->buf);
-}
+/* In the circuits below a wire may be the constant 0 (NULL), and every gate
+ * output gets a fresh row from the evaluation's arena. */
 
 /* One adder position with operands x, y and incoming carry c, any of which
  * may be the constant 0 (NULL).  Only the live operands are combined: one
@@ -620,8 +714,7 @@ static void ev_cell(orc_ev *E, orc_arena *A, const uint32_t *x, const uint32_t *
         if (need_carry) {
             uint32_t *co = arena_new(A);
             if (maj) {
-                orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, x, y, c, co);
-                E->gates++;
+                ev_gate3(E, ORC_MAJ, x, y, c, co);
             } else {
                 uint32_t *g = arena_new(A), *t = arena_new(A);
                 ev_gate(E, ORC_AND, x, y, g);
@@ -642,27 +735,27 @@ static void ev_add_cells(orc_ev *E, orc_arena *A, int32_t w, const uint32_t **x,
         ev_cell(E, A, x[i], y[i], c, i < w - 1, maj, &r[i], &c);
 }
 
-static void copy_out(int32_t w, int64_t W, const uint32_t **r, uint32_t *R)
+static void copy_out(orc_ev *E, int32_t w, const uint32_t **r, uint32_t *R)
 {
+    const int64_t W = E->P->n + 1;
     for (int32_t i = 0; i < w; i++)
-        memcpy(R + i * W, r[i], sizeof(uint32_t) * W);
+        ev_copy(E, r[i], R + i * W);
 }
 
 /* Ripple adder whose carries are single majority gates. */
 static void ev_add_maj(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
 {
     const int64_t W = E->P->n + 1;
-    orc_arena A = {NULL, 0, 0, W};
+    orc_arena *A = &E->A;
     const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
                    **r = malloc(sizeof(*r) * w);
     for (int32_t i = 0; i < w; i++) {
         x[i] = Av + i * W;
         y[i] = Bv + i * W;
     }
-    ev_add_cells(E, &A, w, x, y, 1, r);
-    copy_out(w, W, r, R);
+    ev_add_cells(E, A, w, x, y, 1, r);
+    copy_out(E, w, r, R);
     free(x); free(y); free(r);
-    arena_free(&A);
 }
 
 /* The paper's number-wise addition GPU_n (section V-B-1): R = A; then w
@@ -672,7 +765,7 @@ static void ev_add_maj(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t 
 static void ev_add_nw(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
 {
     const int64_t W = E->P->n + 1;
-    orc_arena A = {NULL, 0, 0, W};
+    orc_arena *A = &E->A;
     const uint32_t **r = malloc(sizeof(*r) * w), **b = malloc(sizeof(*b) * w),
                    **nb = malloc(sizeof(*nb) * w);
     for (int32_t i = 0; i < w; i++) {
@@ -685,9 +778,9 @@ static void ev_add_nw(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *
         for (int32_t i = 0; i < w; i++) {
             if (!b[i])
                 continue;
-            uint32_t *nr = arena_new(&A);
+            uint32_t *nr = arena_new(A);
             if (i + 1 < w) {
-                uint32_t *cy = arena_new(&A);
+                uint32_t *cy = arena_new(A);
                 ev_gate(E, ORC_AND, r[i], b[i], cy);
                 nb[i + 1] = cy;
             }
@@ -697,9 +790,8 @@ static void ev_add_nw(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *
         for (int32_t i = 0; i < w; i++)
             b[i] = nb[i];
     }
-    copy_out(w, W, r, R);
+    copy_out(E, w, r, R);
     free(r); free(b); free(nb);
-    arena_free(&A);
 }
 
 /* Truncated multiplication with tree-based accumulation (section V-B-2):
@@ -711,13 +803,13 @@ static void ev_mul_tree_with(orc_ev *E, int32_t w, const uint32_t *Av, const uin
                              uint32_t *R, int maj)
 {
     const int64_t W = E->P->n + 1;
-    orc_arena A = {NULL, 0, 0, W};
+    orc_arena *A = &E->A;
     const uint32_t **terms = malloc(sizeof(*terms) * w * w), **next = malloc(sizeof(*next) * w * w);
     for (int32_t i = 0; i < w; i++)
         for (int32_t j = 0; j < w; j++) {
             uint32_t *pp = NULL;
             if (j >= i) {
-                pp = arena_new(&A);
+                pp = arena_new(A);
                 ev_gate(E, ORC_AND, Av + (j - i) * W, Bv + i * W, pp);
             }
             terms[i * w + j] = pp;
@@ -726,7 +818,7 @@ static void ev_mul_tree_with(orc_ev *E, int32_t w, const uint32_t *Av, const uin
     while (cnt > 1) {
         int32_t k = 0;
         for (int32_t i = 0; i + 1 < cnt; i += 2, k++)
-            ev_add_cells(E, &A, w, terms + i * w, terms + (i + 1) * w, maj, next + k * w);
+            ev_add_cells(E, A, w, terms + i * w, terms + (i + 1) * w, maj, next + k * w);
         if (cnt & 1) {
             memcpy(next + k * w, terms + (cnt - 1) * w, sizeof(*terms) * w);
             k++;
@@ -734,9 +826,8 @@ static void ev_mul_tree_with(orc_ev *E, int32_t w, const uint32_t *Av, const uin
         memcpy(terms, next, sizeof(*terms) * w * k);
         cnt = k;
     }
-    copy_out(w, W, terms, R);
+    copy_out(E, w, terms, R);
     free(terms); free(next);
-    arena_free(&A);
 }
 
 static void ev_mul_tree(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv, uint32_t *R)
@@ -775,8 +866,7 @@ static const uint32_t *ev_merge(orc_ev *E, orc_arena *A, const uint32_t *g_hi,
     if (!g_hi) {
         ev_gate(E, ORC_AND, k_hi, lo, o);
     } else {
-        orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, g_hi, k_hi, lo, o);
-        E->gates++;
+        ev_gate3(E, ORC_MAJ, g_hi, k_hi, lo, o);
     }
     return o;
 }
@@ -841,17 +931,16 @@ static void ev_add_prefix(orc_ev *E, int32_t w, const uint32_t *Av, const uint32
                           uint32_t *R)
 {
     const int64_t W = E->P->n + 1;
-    orc_arena A = {NULL, 0, 0, W};
+    orc_arena *A = &E->A;
     const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
                    **r = malloc(sizeof(*r) * w);
     for (int32_t i = 0; i < w; i++) {
         x[i] = Av + i * W;
         y[i] = Bv + i * W;
     }
-    ev_prefix_cells(E, &A, w, x, y, r);
-    copy_out(w, W, r, R);
+    ev_prefix_cells(E, A, w, x, y, r);
+    copy_out(E, w, r, R);
     free(x); free(y); free(r);
-    arena_free(&A);
 }
 
 /* Truncated w x w -> w multiplication by a Dadda tree.  Column c (weight
@@ -873,13 +962,13 @@ static int ev_mul_dadda_impl(orc_ev *E, int32_t w, const uint32_t *Av, const uin
 {
     const int64_t W = E->P->n + 1;
     const int32_t cap = 2 * w + 8;
-    orc_arena A = {NULL, 0, 0, W};
+    orc_arena *A = &E->A;
     const uint32_t **col = malloc(sizeof(*col) * w * cap), **nxt = malloc(sizeof(*nxt) * w * cap);
     int32_t *len = calloc(w, sizeof(int32_t)), *nlen = calloc(w, sizeof(int32_t));
     int32_t target[16], nt = 0, ok = 0;
     for (int32_t c = 0; c < w; c++)
         for (int32_t i = 0; i <= c; i++) {
-            uint32_t *o = arena_new(&A);
+            uint32_t *o = arena_new(A);
             ev_gate(E, ORC_AND, Av + (c - i) * W, Bv + i * W, o);
             col[c * cap + len[c]++] = o;
         }
@@ -895,24 +984,23 @@ static int ev_mul_dadda_impl(orc_ev *E, int32_t w, const uint32_t *Av, const uin
                 if (used + need > len[c])
                     goto done;
                 const uint32_t *u = col[c * cap + used], *v = col[c * cap + used + 1];
-                uint32_t *sum = arena_new(&A);
+                uint32_t *sum = arena_new(A);
                 if (need == 2) {
                     ev_gate(E, ORC_XOR, u, v, sum);
                     if (c + 1 < w) {
-                        uint32_t *cy = arena_new(&A);
+                        uint32_t *cy = arena_new(A);
                         ev_gate(E, ORC_AND, u, v, cy);
                         nxt[(c + 1) * cap + nlen[c + 1]++] = cy;
                     }
                     h -= 1;
                 } else {
                     const uint32_t *z = col[c * cap + used + 2];
-                    uint32_t *uv = arena_new(&A);
+                    uint32_t *uv = arena_new(A);
                     ev_gate(E, ORC_XOR, u, v, uv);
                     ev_gate(E, ORC_XOR, uv, z, sum);
                     if (c + 1 < w) {
-                        uint32_t *cy = arena_new(&A);
-                        orc_gate3(E->P, E->bk, E->ksk, ORC_MAJ, u, v, z, cy);
-                        E->gates++;
+                        uint32_t *cy = arena_new(A);
+                        ev_gate3(E, ORC_MAJ, u, v, z, cy);
                         nxt[(c + 1) * cap + nlen[c + 1]++] = cy;
                     }
                     h -= 2;
@@ -943,21 +1031,21 @@ static int ev_mul_dadda_impl(orc_ev *E, int32_t w, const uint32_t *Av, const uin
                 y[c] = col[c * cap + 1];
         }
         if (fits) {
-            ev_prefix_cells(E, &A, w, x, y, r);
-            copy_out(w, W, r, R);
+            ev_prefix_cells(E, A, w, x, y, r);
+            copy_out(E, w, r, R);
             ok = 1;
         }
         free(x); free(y); free(r);
     }
 done:
     free(col); free(nxt); free(len); free(nlen);
-    arena_free(&A);
     return ok ? 0 : -1;
 }
 
 static void ev_mul_dadda(orc_ev *E, int32_t w, const uint32_t *Av, const uint32_t *Bv,
                          uint32_t *R)
 {
+    /* (on failure no gate task reads or writes R, so it is cleared here) */
     if (ev_mul_dadda_impl(E, w, Av, Bv, R) != 0)
         memset(R, 0, sizeof(uint32_t) * (E->P->n + 1) * w);
 }
@@ -1092,41 +1180,36 @@ static void ev_karatsuba(orc_ev *E, orc_arena *A, int32_t n, const uint32_t **X,
 typedef void (*orc_full_fn)(orc_ev *, orc_arena *, int32_t, const uint32_t **, const uint32_t **,
                             const uint32_t **);
 
-/* Batched full products: A, B [batch][w][n+1] -> R [batch][2w][n+1]. */
+/* Batched full products: A, B [batch][w][n+1] -> R [batch][2w][n+1].  One
+ * thread builds every instance's gate tasks, the team runs them; they have
+ * all finished when the parallel region ends. */
 static int64_t run_full(orc_full_fn fn, const orc_params *P, const uint32_t *bk,
                         const uint32_t *ksk, int32_t w, int64_t batch, const uint32_t *Av,
                         const uint32_t *Bv, uint32_t *R, int32_t nthreads)
 {
     const int64_t W = P->n + 1, num = W * w;
-    int64_t total = 0;
-#ifdef _OPENMP
-    if (nthreads <= 0)
-        nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
-#endif
+    orc_ev *E = ev_new_many(P, bk, ksk, batch);
+    nthreads = ev_threads(nthreads);
+#pragma omp parallel num_threads(nthreads)
+#pragma omp single
     for (int64_t b = 0; b < batch; b++) {
-        orc_ev E = {P, bk, ksk, 0};
-        orc_arena A = {NULL, 0, 0, W};
         const uint32_t **x = malloc(sizeof(*x) * w), **y = malloc(sizeof(*y) * w),
                        **z = malloc(sizeof(*z) * 2 * w);
         for (int32_t i = 0; i < w; i++) {
             x[i] = Av + b * num + i * W;
             y[i] = Bv + b * num + i * W;
         }
-        fn(&E, &A, w, x, y, z);
+        fn(&E[b], &E[b].A, w, x, y, z);
         for (int32_t i = 0; i < 2 * w; i++) {
+            uint32_t *o = R + 2 * b * num + i * W;
             if (z[i])
-                memcpy(R + 2 * b * num + i * W, z[i], sizeof(uint32_t) * W);
-            else {  /* a constant-0 bit: the trivial sample (0, ..., 0, -1/8) */
-                memset(R + 2 * b * num + i * W, 0, sizeof(uint32_t) * W);
-                R[2 * b * num + i * W + P->n] = (uint32_t)-(1u << 29);
-            }
+                ev_copy(&E[b], z[i], o);
+            else
+                ev_const0(&E[b], o);   /* a constant-0 bit */
         }
         free(x); free(y); free(z);
-        arena_free(&A);
-        total += E.gates;
     }
-    return total;
+    return ev_free_many(E, batch);
 }
 
 int64_t orc_mul_full(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
@@ -1143,45 +1226,11 @@ int64_t orc_mul_karatsuba(const orc_params *P, const uint32_t *bk, const uint32_
     return run_full(ev_karatsuba, P, bk, ksk, w, batch, A, B, R, nthreads);
 }
 
-/* Batched circuit entry points: instances are independent and are spread
- * over threads; each instance is evaluated gate by gate in program order.
- * Return the number of bootstrapped gates evaluated. */
-int64_t orc_add(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
-                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
-{
-    const int64_t num = (int64_t)(P->n + 1) * w;
-    int64_t total = 0;
-#ifdef _OPENMP
-    if (nthreads <= 0)
-        nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
-#endif
-    for (int64_t b = 0; b < batch; b++) {
-        orc_ev E = {P, bk, ksk, 0};
-        ev_add(&E, w, A + b * num, B + b * num, R + b * num);
-        total += E.gates;
-    }
-    return total;
-}
-
-int64_t orc_mul(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
-                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
-{
-    const int64_t num = (int64_t)(P->n + 1) * w;
-    int64_t total = 0;
-#ifdef _OPENMP
-    if (nthreads <= 0)
-        nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
-#endif
-    for (int64_t b = 0; b < batch; b++) {
-        orc_ev E = {P, bk, ksk, 0};
-        ev_mul(&E, w, A + b * num, B + b * num, R + b * num);
-        total += E.gates;
-    }
-    return total;
-}
-
+/* Batched circuit entry points: one thread builds the gate tasks of every
+ * instance in program order and the team of nthreads threads runs them, so
+ * independent gates -- of one instance or of different instances -- run in
+ * parallel; they have all finished when the parallel region ends.  Return
+ * the number of bootstrapped gates evaluated. */
 typedef void (*orc_circuit_fn)(orc_ev *, int32_t, const uint32_t *, const uint32_t *, uint32_t *);
 
 static int64_t run_batched(orc_circuit_fn fn, const orc_params *P, const uint32_t *bk,
@@ -1189,18 +1238,25 @@ static int64_t run_batched(orc_circuit_fn fn, const orc_params *P, const uint32_
                            const uint32_t *B, uint32_t *R, int32_t nthreads)
 {
     const int64_t num = (int64_t)(P->n + 1) * w;
-    int64_t total = 0;
-#ifdef _OPENMP
-    if (nthreads <= 0)
-        nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
-#endif
-    for (int64_t b = 0; b < batch; b++) {
-        orc_ev E = {P, bk, ksk, 0};
-        fn(&E, w, A + b * num, B + b * num, R + b * num);
-        total += E.gates;
-    }
-    return total;
+    orc_ev *E = ev_new_many(P, bk, ksk, batch);
+    nthreads = ev_threads(nthreads);
+#pragma omp parallel num_threads(nthreads)
+#pragma omp single
+    for (int64_t b = 0; b < batch; b++)
+        fn(&E[b], w, A + b * num, B + b * num, R + b * num);
+    return ev_free_many(E, batch);
+}
+
+int64_t orc_add(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
+{
+    return run_batched(ev_add, P, bk, ksk, w, batch, A, B, R, nthreads);
+}
+
+int64_t orc_mul(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
+                int64_t batch, const uint32_t *A, const uint32_t *B, uint32_t *R, int32_t nthreads)
+{
+    return run_batched(ev_mul, P, bk, ksk, w, batch, A, B, R, nthreads);
 }
 
 int64_t orc_add_maj(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int32_t w,
@@ -1250,18 +1306,13 @@ int64_t orc_matvec(const orc_params *P, const uint32_t *bk, const uint32_t *ksk,
                    int32_t nthreads)
 {
     const int64_t num = (int64_t)(P->n + 1) * w;
-    int64_t total = 0;
-#ifdef _OPENMP
-    if (nthreads <= 0)
-        nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
-#endif
-    for (int32_t r = 0; r < rows; r++) {
-        orc_ev E = {P, bk, ksk, 0};
-        ev_matvec_row(&E, w, cols, M + (int64_t)r * cols * num, v, Y + r * num);
-        total += E.gates;
-    }
-    return total;
+    orc_ev *E = ev_new_many(P, bk, ksk, rows);
+    nthreads = ev_threads(nthreads);
+#pragma omp parallel num_threads(nthreads)
+#pragma omp single
+    for (int32_t r = 0; r < rows; r++)
+        ev_matvec_row(&E[r], w, cols, M + (int64_t)r * cols * num, v, Y + r * num);
+    return ev_free_many(E, rows);
 }
 
 int32_t orc_max_threads(void)
