@@ -150,6 +150,33 @@ int tfhe_blind_rotate_extract(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *
                               const int32_t *b, int32_t *big, size_t count, void *stream);
 int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count, void *stream);
 
+/* The external product's negacyclic products on the tensor pipe, exposed to
+ * measure the alternative to the NTT (the product inside the CMux of the
+ * TFHE blind rotation, paper section II-A): for `count` bootstraps at one
+ * CMux step, out[m][p][k] = sum_r (d_r[m] * BK[r][p])[k] in
+ * Z[X]/(X^1024 + 1) mod 2^32, r < 4, p < 2 -- the 8 products the NTT path
+ * computes per CMux -- as tcgen05 matrix products of limb-split bf16
+ * operands with exact fp32 sums (digits split in 2 limbs, key words in 4
+ * balanced bytes).  The blind-rotation kernels do not use it: on GB300 it
+ * is slower than the NTT (measurements in the design notes).
+ *   tfhe_tc_prepare_key: bk_rows = device uint32 [4 rows][2 polys][1024]
+ *     (one TGSW key sample in coefficient form, row r = c l + j) ->
+ *     key_ops, a caller-owned device buffer of tfhe_tc_key_bytes() bytes
+ *     (64 MB, 16-byte aligned): the transposed negacyclic Toeplitz operand,
+ *     4 bytes x 2048 x 4096 bf16.
+ *   tfhe_cmux_products_tc: digits = device int32 [count][4][1024], every
+ *     digit in [-512, 511] (out-of-range digits set status bit 0 and give
+ *     undefined outputs); digit_ops = caller-owned device scratch of
+ *     tfhe_tc_digit_bytes(count) bytes (16-byte aligned); out = device
+ *     uint32 [count][2][1024].  count must be a multiple of 128 (at most
+ *     128 x 65535); TFHE_EINVAL otherwise.  Asynchronous on `stream`; a
+ *     wait that runs out sets status bit 2. */
+size_t tfhe_tc_key_bytes(void);
+size_t tfhe_tc_digit_bytes(size_t count);
+int tfhe_tc_prepare_key(tfhe_ctx *ctx, const uint32_t *bk_rows, void *key_ops, void *stream);
+int tfhe_cmux_products_tc(tfhe_ctx *ctx, const int32_t *digits, const void *key_ops,
+                          void *digit_ops, uint32_t *out, size_t count, void *stream);
+
 /* Same computation and result as tfhe_bootstrap_gates, for callers that
  * cannot let the library allocate device memory while they call it
  * (runtimes that reserve all device memory up front, serving loops that
@@ -289,6 +316,9 @@ typedef enum {
                              /*    rows staged in shared memory by bulk copies),    */
                              /*    1, 2, 4, .. 32 = direct kernel with that j-split, */
                              /*    or 0 (default): autotuned, else by batch size    */
+    TFHE_OPT_TEST_FREE_HBM = 8,/* test hook for serving admission, 0 (default) off: */
+                             /*    a serving loop started afterwards takes this     */
+                             /*    many bytes as the device's free memory           */
     TFHE_OPT_TEST_KS_STALL = 7 /* test hook for the timeout path, 0 (default) off:  */
                              /*    1 makes every stage of the tiled key switch also */
                              /*    wait on an mbarrier that nothing completes, so   */
@@ -341,11 +371,23 @@ typedef struct {
     uint64_t in_flight;      /* admitted, not finished                       */
     uint64_t queued;         /* waiting for pool rows                        */
     double wall_ms;          /* first submit to last completion              */
+    uint64_t pool_bytes;     /* device memory the ciphertext pool holds now  */
+    uint64_t pool_cap_bytes; /* the most it may grow to (the caller's cap, or */
+                             /* the device's memory)                         */
+    uint64_t pool_grows;     /* times admission grew the pool                */
+    uint64_t admitted_busy;  /* requests admitted while others were running  */
 } tfhe_serve_info;
 
 /* Start the request loop on the context's device: a worker thread with its
- * own stream and a ciphertext pool of hbm_budget_bytes (requests are
- * admitted, in arrival order, when their rows fit).  Each iteration runs the
+ * own stream and a ciphertext pool.  Requests are admitted in arrival order
+ * when their rows (inputs and every gate output, 2 KB each) fit in the
+ * pool; when they do not, the pool grows by mapping more device memory, as
+ * long as the device's free HBM (cudaMemGetInfo) stays 1 GiB above the
+ * growth and the pool stays within hbm_budget_bytes (0: no cap but the
+ * device).  Otherwise the request waits until finished requests free rows.
+ * The pool is one reserved range of device addresses mapped in steps
+ * (driver virtual memory management); where that is unavailable it is one
+ * fixed allocation of the cap (or of half the free memory, at most 32 GB).  Each iteration runs the
  * next level of every admitted request as one batched bootstrap, up to
  * max_batch_gates gates (0: a default of 8 waves of the GPU); requests that
  * arrive meanwhile join the next iteration.  While serving, the context

@@ -59,6 +59,11 @@ EXPORTS = {
     "tfhe_blind_rotate_extract": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t,
                                                                         ctypes.c_void_p]),
     "tfhe_keyswitch": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "tfhe_tc_key_bytes": (ctypes.c_size_t, []),
+    "tfhe_tc_digit_bytes": (ctypes.c_size_t, [ctypes.c_size_t]),
+    "tfhe_tc_prepare_key": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "tfhe_cmux_products_tc": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_size_t,
+                                                                     ctypes.c_void_p]),
     "tfhe_add_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
                    + [ctypes.c_size_t, ctypes.c_void_p]),
     "tfhe_mul_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
@@ -107,7 +112,7 @@ EXPORTS = {
 GATE, ADD, MUL, MATVEC, ADD_MAJ, ADD_NW, MUL_TREE, MUL_FULL, MUL_KARATSUBA, MUL_TREE_MAJ, \
     ADD_PREFIX, MUL_DADDA = range(12)
 OPT_GRAPHS, OPT_PER_GATE, OPT_PROFILE, OPT_BR_GROUP, OPT_SCHEDULE, OPT_LEVEL_WIDTH, \
-    OPT_KS_KERNEL, OPT_TEST_KS_STALL = range(8)
+    OPT_KS_KERNEL, OPT_TEST_KS_STALL, OPT_TEST_FREE_HBM = range(9)
 KS_TILED = 64   # OPT_KS_KERNEL value of the tiled key-switch kernel
 SCHED_ASAP, SCHED_BALANCED = 0, 1
 
@@ -127,7 +132,9 @@ class CRequest(ctypes.Structure):
 class CServeInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "gates",
                                                "iterations", "in_flight", "queued")] + \
-               [("wall_ms", ctypes.c_double)]
+               [("wall_ms", ctypes.c_double)] + \
+               [(f, ctypes.c_uint64) for f in ("pool_bytes", "pool_cap_bytes", "pool_grows",
+                                               "admitted_busy")]
 
 
 _lib = None
@@ -314,6 +321,28 @@ class Context:
         self._c(lib().tfhe_keyswitch(self._h, _dev(big, torch.int32), _dev(out, torch.int32),
                                      big.shape[0], _stream(stream)))
 
+    def tc_prepare_key(self, bk_rows, key_ops, stream=None):
+        """bk_rows: uint32 (as int32) [4][2][1024] device tensor -> key_ops
+        (uint8 device tensor of tc_key_bytes() bytes)."""
+        import torch
+        if bk_rows.numel() < 4 * 2 * 1024 or key_ops.numel() * key_ops.element_size() < \
+                lib().tfhe_tc_key_bytes():
+            raise TFHEError(-1, "tc_prepare_key: buffer too small")
+        self._c(lib().tfhe_tc_prepare_key(self._h, _dev(bk_rows, torch.int32), _dev(key_ops),
+                                          _stream(stream)))
+
+    def cmux_products_tc(self, digits, key_ops, digit_ops, out, stream=None):
+        """digits: int32 [count][4][1024]; out: int32 (uint32 words)
+        [count][2][1024]; count a multiple of 128."""
+        import torch
+        count = digits.shape[0]
+        if digits.numel() < count * 4096 or out.numel() < count * 2048 or \
+                digit_ops.numel() * digit_ops.element_size() < lib().tfhe_tc_digit_bytes(count):
+            raise TFHEError(-1, "cmux_products_tc: buffer too small")
+        self._c(lib().tfhe_cmux_products_tc(self._h, _dev(digits, torch.int32), _dev(key_ops),
+                                            _dev(digit_ops), _dev(out, torch.int32), count,
+                                            _stream(stream)))
+
     def add_n(self, width, A, B, R, stream=None):
         import torch
         batch = A.shape[0]
@@ -431,6 +460,16 @@ def schedule_info(jobs, policy=1, target=0):
                                     ctypes.c_void_p(widths.ctypes.data), depth.value,
                                     ctypes.byref(depth), ctypes.byref(gates)))
     return widths[:depth.value], int(gates.value)
+
+
+def tc_key_bytes() -> int:
+    """Bytes of the tensor-pipe key operand of one CMux step."""
+    return int(lib().tfhe_tc_key_bytes())
+
+
+def tc_digit_bytes(count) -> int:
+    """Bytes of the tensor-pipe digit operand scratch for `count` bootstraps."""
+    return int(lib().tfhe_tc_digit_bytes(count))
 
 
 def circuit_info(kind, width, rows=0, cols=0):

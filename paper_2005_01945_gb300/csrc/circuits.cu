@@ -1242,6 +1242,11 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
             return fail(ctx, TFHE_EINVAL, "TFHE_OPT_LEVEL_WIDTH must be >= 0");
         C.level_width = (long)value;
         return TFHE_OK;
+    case TFHE_OPT_TEST_FREE_HBM:
+        if (value < 0)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_TEST_FREE_HBM must be >= 0");
+        ctx->test_free_hbm = (size_t)value;
+        return TFHE_OK;
     case TFHE_OPT_TEST_KS_STALL:
         ctx->keys.ks_stall = value != 0;
         invalidate_graphs(ctx);

@@ -24,6 +24,7 @@ struct tfhe_ctx {
     tgb::DevKeys keys{};
     std::string err;
     uint64_t launches = 0;           // kernels issued (graph nodes count per replay)
+    size_t test_free_hbm = 0;        // test hook: serving takes this as the free HBM
     tgb::CircuitCache *circuits = nullptr;
     tgb::Server *server = nullptr;
 };

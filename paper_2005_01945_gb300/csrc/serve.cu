@@ -2,8 +2,9 @@
 //
 // Requests (one circuit instance each: a gate, an add, a mul, a matvec) are
 // submitted from any host thread.  A worker thread owns one CUDA stream and
-// a device ciphertext pool sized by an HBM budget; it admits queued requests
-// in arrival order whenever their rows fit in the pool (first fit), copies
+// a device ciphertext pool; it admits queued requests in arrival order
+// whenever their rows fit in the pool (first fit), growing the pool from
+// the device's free HBM (under the caller's cap) when they do not, copies
 // their inputs in, and then runs iterations: one iteration is one batched
 // blind-rotation launch plus one key-switch launch over the next level of
 // every admitted request (oldest first, up to a gate cap).  A request's
@@ -29,6 +30,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda.h>
+
 #include "netlist.h"
 #include "runtime.h"
 
@@ -50,6 +53,23 @@ struct RowAlloc {
         free_.clear();
         if (cap > 0)
             free_[0] = cap;
+    }
+    // Rows the pool gained at its end become free (merged with a free tail).
+    void grow(long cap)
+    {
+        if (cap > capacity) {
+            const long old = capacity;
+            capacity = cap;
+            release(old, cap - old);
+        }
+    }
+    // Free rows at the end of the pool.
+    long tail() const
+    {
+        if (free_.empty())
+            return 0;
+        auto last = std::prev(free_.end());
+        return last->first + last->second == capacity ? last->second : 0;
     }
     long alloc(long n)
     {
@@ -78,6 +98,187 @@ struct RowAlloc {
                 free_.erase(it);
             }
         }
+    }
+};
+
+// The ciphertext pool: one reserved range of device virtual addresses (the
+// caller's cap, or the device's memory) into which physical HBM is mapped
+// in steps as admission needs it, through the driver's virtual memory
+// management (entry points looked up through the runtime, no link against
+// the driver).  The base address never moves, so every row index the
+// kernels are given stays valid while the pool grows.  Without those entry
+// points the pool is one cudaMalloc of the cap (or of the free memory minus
+// the headroom), fixed for the whole session.
+struct VmmApi {
+    CUresult (*reserve)(CUdeviceptr *, size_t, size_t, CUdeviceptr, unsigned long long);
+    CUresult (*addr_free)(CUdeviceptr, size_t);
+    CUresult (*create)(CUmemGenericAllocationHandle *, size_t, const CUmemAllocationProp *,
+                       unsigned long long);
+    CUresult (*release)(CUmemGenericAllocationHandle);
+    CUresult (*map)(CUdeviceptr, size_t, size_t, CUmemGenericAllocationHandle, unsigned long long);
+    CUresult (*unmap)(CUdeviceptr, size_t);
+    CUresult (*set_access)(CUdeviceptr, size_t, const CUmemAccessDesc *, size_t);
+    CUresult (*granularity)(size_t *, const CUmemAllocationProp *,
+                            CUmemAllocationGranularity_flags);
+};
+
+static const VmmApi *vmm_api()
+{
+    static std::once_flag once;
+    static VmmApi api{};
+    static bool ok = false;
+    std::call_once(once, [] {
+        struct {
+            const char *name;
+            void **slot;
+        } fns[] = {{"cuMemAddressReserve", (void **)&api.reserve},
+                   {"cuMemAddressFree", (void **)&api.addr_free},
+                   {"cuMemCreate", (void **)&api.create},
+                   {"cuMemRelease", (void **)&api.release},
+                   {"cuMemMap", (void **)&api.map},
+                   {"cuMemUnmap", (void **)&api.unmap},
+                   {"cuMemSetAccess", (void **)&api.set_access},
+                   {"cuMemGetAllocationGranularity", (void **)&api.granularity}};
+        ok = true;
+        for (auto &f : fns) {
+            cudaDriverEntryPointQueryResult q{};
+            if (cudaGetDriverEntryPointByVersion(f.name, f.slot, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !*f.slot)
+                ok = false;
+        }
+        (void)cudaGetLastError();
+    });
+    return ok ? &api : nullptr;
+}
+
+// Free HBM that growing the pool always leaves to other allocations (the
+// iteration buffers, the caller, other processes on the device).
+constexpr size_t kPoolHeadroom = 1ull << 30;
+constexpr size_t kRowBytes = kLweStride * sizeof(int32_t);
+
+struct GrowPool {
+    const VmmApi *api = nullptr;   // null: fixed cudaMalloc pool
+    int device = 0;
+    CUdeviceptr base = 0;
+    size_t limit = 0;              // the cap in bytes (the device's memory if none)
+    size_t reserved = 0, mapped = 0, gran = 0;
+    std::vector<std::pair<CUmemGenericAllocationHandle, size_t>> chunks;
+    int32_t *ptr() const { return reinterpret_cast<int32_t *>(base); }
+    long rows() const { return (long)(std::min(mapped, limit) / kRowBytes); }
+    long max_rows() const { return (long)(limit / kRowBytes); }
+
+    CUmemAllocationProp prop() const
+    {
+        CUmemAllocationProp p{};
+        p.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+        p.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+        p.location.id = device;
+        return p;
+    }
+
+    // Maps `bytes` (a multiple of the granularity) more at the end.
+    bool map_more(size_t bytes)
+    {
+        if (!api || bytes == 0 || mapped + bytes > reserved)
+            return false;
+        const CUmemAllocationProp pr = prop();
+        CUmemGenericAllocationHandle h{};
+        if (api->create(&h, bytes, &pr, 0) != CUDA_SUCCESS)
+            return false;
+        if (api->map(base + mapped, bytes, 0, h, 0) != CUDA_SUCCESS) {
+            api->release(h);
+            return false;
+        }
+        CUmemAccessDesc acc{};
+        acc.location = pr.location;
+        acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+        if (api->set_access(base + mapped, bytes, &acc, 1) != CUDA_SUCCESS) {
+            api->unmap(base + mapped, bytes);
+            api->release(h);
+            return false;
+        }
+        chunks.push_back({h, bytes});
+        mapped += bytes;
+        return true;
+    }
+
+    // Reserves cap bytes of addresses (0: the device's memory) and maps the
+    // first step; falls back to a fixed cudaMalloc pool.
+    cudaError_t init(int dev, size_t cap, size_t free_bytes)
+    {
+        device = dev;
+        size_t fr = 0, total = 0;
+        cudaError_t e = cudaMemGetInfo(&fr, &total);
+        if (e != cudaSuccess)
+            return e;
+        api = vmm_api();
+        const CUmemAllocationProp pr = prop();
+        if (api && api->granularity(&gran, &pr, CU_MEM_ALLOC_GRANULARITY_RECOMMENDED) !=
+                       CUDA_SUCCESS)
+            api = nullptr;
+        limit = cap ? cap : total;
+        if (api) {
+            reserved = (limit + gran - 1) / gran * gran;
+            if (api->reserve(&base, reserved, gran, 0, 0) != CUDA_SUCCESS) {
+                api = nullptr;
+                base = 0;
+            }
+        }
+        if (api) {
+            // first step: 8 MB (or one granule when the device is short)
+            size_t first = std::min(reserved, std::max<size_t>(gran, (8ull << 20) / gran * gran));
+            if (free_bytes < first + kPoolHeadroom)
+                first = gran;
+            return map_more(first) ? cudaSuccess : cudaErrorMemoryAllocation;
+        }
+        // fixed pool: the cap, or half the free memory (at most 32 GB)
+        size_t bytes = cap ? cap : std::min<size_t>(free_bytes / 2, 32ull << 30);
+        bytes = std::max(bytes / kRowBytes, (size_t)64) * kRowBytes;
+        void *p = nullptr;
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess)
+            return e;
+        base = reinterpret_cast<CUdeviceptr>(p);
+        limit = reserved = mapped = bytes;
+        return cudaSuccess;
+    }
+
+    // Grows so that `extra_rows` more rows exist at the end, if the device's
+    // free memory (free_bytes) keeps the headroom and the cap allows.  Steps
+    // double the mapping (at most 8 GB at a time), or are just what the
+    // request needs when free memory is short.
+    bool grow(long extra_rows, size_t free_bytes)
+    {
+        if (!api || extra_rows <= 0)
+            return false;
+        const size_t need = ((size_t)extra_rows * kRowBytes + gran - 1) / gran * gran;
+        if (mapped + need > reserved || rows() + extra_rows > max_rows())
+            return false;
+        const size_t dbl = std::min<size_t>(std::max<size_t>(mapped, 64ull << 20), 8ull << 30);
+        size_t bytes = std::min(std::max(need, (dbl + gran - 1) / gran * gran), reserved - mapped);
+        if (free_bytes < bytes + kPoolHeadroom)
+            bytes = need;   // only what this request needs
+        if (free_bytes < bytes + kPoolHeadroom)
+            return false;   // the device is short: wait for rows to free up
+        return map_more(bytes);
+    }
+
+    void release()
+    {
+        if (api) {
+            if (mapped)
+                api->unmap(base, mapped);
+            for (auto &c : chunks)
+                api->release(c.first);
+            if (base)
+                api->addr_free(base, reserved);
+        } else if (base) {
+            cudaFree(reinterpret_cast<void *>(base));
+        }
+        chunks.clear();
+        base = 0;
+        mapped = reserved = 0;
     }
 };
 
@@ -111,8 +312,11 @@ struct Server {
     std::condition_variable cv;
     bool stopping = false;
     cudaStream_t st = nullptr;
-    int32_t *pool = nullptr;
-    long pool_rows = 0;
+    GrowPool gp;
+    int32_t *pool = nullptr;       // gp's base
+    long pool_rows = 0;            // rows mapped now (grows; worker thread only)
+    long max_rows = 0;             // rows the pool may ever hold
+    size_t test_free_hbm = 0;      // test hook: taken as the device's free memory
     RowAlloc rows;
     int32_t *big = nullptr;
     long big_rows = 0, max_batch = 0;
@@ -225,14 +429,31 @@ static void srv_loop(Server *Sp)
                 if (S.stopping && S.queue.empty())
                     break;
             }
-            // admission in arrival order while rows fit
+            // admission in arrival order while rows fit; the pool grows from
+            // the device's free memory when they do not
             while (!S.queue.empty()) {
                 SrvReq *r = S.queue.front();
-                const long base = S.rows.alloc(r->inst_rows);
+                long base = S.rows.alloc(r->inst_rows);
+                if (base < 0) {
+                    size_t fr = 0, total = 0;
+                    if (S.test_free_hbm)
+                        fr = S.test_free_hbm;
+                    else if (cudaMemGetInfo(&fr, &total) != cudaSuccess)
+                        (void)cudaGetLastError();
+                    if (S.gp.grow(r->inst_rows - S.rows.tail(), fr)) {
+                        S.pool_rows = S.gp.rows();
+                        S.rows.grow(S.pool_rows);
+                        S.stats.pool_grows++;
+                        S.stats.pool_bytes = S.gp.mapped;
+                        base = S.rows.alloc(r->inst_rows);
+                    }
+                }
                 if (base < 0)
                     break;
                 r->base = base;
                 r->state = 1;
+                if (!S.running.empty() || S.it[0].busy || S.it[1].busy)
+                    S.stats.admitted_busy++;
                 S.queue.pop_front();
                 admitted.push_back(r);
                 S.running.push_back(r);
@@ -390,7 +611,9 @@ void release_serving(tfhe_ctx *ctx)
         if (I.ev)
             cudaEventDestroy(I.ev);
     }
-    cudaFree(S->pool);
+    if (S->st)
+        cudaStreamSynchronize(S->st);
+    S->gp.release();
     cudaFree(S->big);
     if (S->st)
         cudaStreamDestroy(S->st);
@@ -414,18 +637,33 @@ int tfhe_serve_start(tfhe_ctx *ctx, size_t hbm_budget_bytes, size_t max_batch_ga
         return fail(ctx, TFHE_EBUSY, "serving already started");
     if (!ctx->keys_loaded)
         return fail(ctx, TFHE_EINVAL, "keys not set");
-    const long rows = (long)(hbm_budget_bytes / (kLweStride * sizeof(int32_t)));
-    if (rows < 64)
+    if (hbm_budget_bytes && hbm_budget_bytes / kRowBytes < 64)
         return fail(ctx, TFHE_EINVAL, "HBM budget too small (%zu bytes)", hbm_budget_bytes);
+    // 0: no cap but the device's memory; row indices are 32-bit
+    const size_t cap = hbm_budget_bytes ? std::min<size_t>(hbm_budget_bytes,
+                                                           (size_t)(1L << 30) * kRowBytes)
+                                        : 0;
     DeviceGuard dg(ctx->device);
     Server *S = new Server();
     S->ctx = ctx;
-    S->pool_rows = std::min(rows, (long)(1L << 30));
+    S->test_free_hbm = ctx->test_free_hbm;
     S->max_batch = max_batch_gates ? (long)max_batch_gates : 8L * ctx->br_grid;
     S->big_rows = S->max_batch;
-    cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    size_t fr = 0, total = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &total);
+    if (S->test_free_hbm)
+        fr = S->test_free_hbm;
     if (e == cudaSuccess)
-        e = cudaMalloc(&S->pool, S->pool_rows * kLweStride * sizeof(int32_t));
+        e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = S->gp.init(ctx->device, cap, fr);
+    if (e == cudaSuccess) {
+        S->pool = S->gp.ptr();
+        S->pool_rows = S->gp.rows();
+        S->max_rows = S->gp.max_rows();
+        S->stats.pool_bytes = S->gp.mapped;
+        S->stats.pool_cap_bytes = S->gp.reserved;
+    }
     if (e == cudaSuccess)
         e = cudaMalloc(&S->big, S->big_rows * kBigStride * sizeof(int32_t));
     for (Iter &I : S->it)
@@ -472,10 +710,10 @@ int tfhe_serve_submit(tfhe_ctx *ctx, const tfhe_request *req, uint64_t *id)
         delete r;
         return fail(ctx, S->fatal, "serving stopped after an error");
     }
-    if (r->inst_rows > S->pool_rows) {
+    if (r->inst_rows > S->max_rows) {
         delete r;
-        return fail(ctx, TFHE_ENOMEM, "request needs %ld rows, pool has %ld", (long)nl->wires(),
-                    S->pool_rows);
+        return fail(ctx, TFHE_ENOMEM, "request needs %ld rows, the pool can hold %ld",
+                    (long)nl->wires(), S->max_rows);
     }
     r->id = S->next_id++;
     r->t_submit = now_ms();

@@ -2,10 +2,13 @@
 
 Bit-exact comparisons with the oracle use the real ring (N = 1024, same
 gadget and key switch) with LWE dimension n = 16, which the library takes
-at runtime; the oracle's bootstrap is then ~30x cheaper, so full-width
-32-bit circuits can be compared word for word.  Full-size workloads at
-n = 500 are checked by decryption on every output and bit-exactly on the
-outputs the oracle computes one by one (depth-1 gates on fresh inputs).
+at runtime; the oracle's bootstrap is then ~30x cheaper, so every circuit
+kind can be compared word for word.  The full-size workloads at n = 500
+(256 32-bit additions, 64 + 64 multiplications, the 16x16 matvec) are run
+as one schedule each, exactly as the benchmark runs them; every output is
+checked by decryption, and sampled whole instances (16 additions, one
+16-bit and one 32-bit multiplication, one matvec output row) are
+recomputed by the oracle gate by gate and compared word for word.
 """
 import numpy as np
 import pytest
@@ -225,7 +228,11 @@ def test_shallow_circuits_full_parameters_decrypt(full):
 
 
 def test_config2_mul16_mul32_mixed(full):
-    """64 16-bit and 64 32-bit multiplications in one schedule."""
+    """64 16-bit and 64 32-bit multiplications in one schedule (222,208
+    bootstraps, uneven depths 56 and 120), n = 500: every product decrypts
+    correctly, and one 16-bit and one 32-bit instance are recomputed by the
+    oracle gate by gate (648 + 2,824 bootstraps, 120 levels deep) with every
+    output ciphertext bit-exact."""
     E = full
     api = E.api
     a16, b16 = synth.int_pairs(64, 16, synth.MASTER_SEED + 2, "mul16")
@@ -238,25 +245,36 @@ def test_config2_mul16_mul32_mixed(full):
     E.ctx.run_jobs([dict(kind=api.MUL, width=16, batch=64, in0=d16a, in1=d16b, out=R16),
                     dict(kind=api.MUL, width=32, batch=64, in0=d32a, in1=d32b, out=R32)])
     g16, g32 = E.host(R16), E.host(R32)
+    assert E.ctx.status() == 0
     assert np.array_equal(E.dec_ints(g16), (a16 * b16) % (1 << 16))
     assert np.array_equal(E.dec_ints(g32), (a32 * b32) % (1 << 32))
-    idx = np.array([3, 60])
-    want = E.orc.gates(E.P, E.obk, E.oksk, np.full(2, 1, np.uint8), o32a[idx, 0], o32b[idx, 0])
-    assert np.array_equal(g32[idx, 0], want)
+    i16, i32 = 9, 41
+    want16, n16 = E.orc.mul(E.P, E.obk, E.oksk, 16, o16a[[i16]], o16b[[i16]])
+    want32, n32 = E.orc.mul(E.P, E.obk, E.oksk, 32, o32a[[i32]], o32b[[i32]])
+    assert (n16, n32) == (648, 2824)
+    assert np.array_equal(g16[i16], want16[0])
+    assert np.array_equal(g32[i32], want32[0])
 
 
 def test_config3_matvec16(full):
-    """16x16 matrix times 16-vector, 16-bit (183,648 bootstraps)."""
+    """16x16 matrix times 16-vector, 16-bit (183,648 bootstraps), n = 500:
+    every output decrypts correctly, and one full output row (16 products
+    and the adder tree, 11,478 bootstraps) is recomputed by the oracle gate
+    by gate with all 16 output ciphertexts bit-exact."""
     E = full
     M = synth.random_uints((16, 16), 16, synth.MASTER_SEED + 3, "M")
     v = synth.random_uints(16, 16, synth.MASTER_SEED + 3, "v")
-    dM, _ = E.enc_ints(M, 16, synth.MASTER_SEED + 3, "M")
-    dv, _ = E.enc_ints(v, 16, synth.MASTER_SEED + 3, "v")
+    dM, oM = E.enc_ints(M, 16, synth.MASTER_SEED + 3, "M")
+    dv, ov = E.enc_ints(v, 16, synth.MASTER_SEED + 3, "v")
     y = E.out((16, 16))
     E.ctx.matvec(16, dM, dv, y)
     got = E.host(y)
-    assert np.array_equal(E.dec_ints(got), (M * v[None, :]).sum(axis=1) % (1 << 16))
     assert E.ctx.status() == 0
+    assert np.array_equal(E.dec_ints(got), (M * v[None, :]).sum(axis=1) % (1 << 16))
+    r = 6
+    want, gates = E.orc.matvec(E.P, E.obk, E.oksk, 16, np.ascontiguousarray(oM[[r]]), ov)
+    assert gates == 16 * 648 + 15 * 74
+    assert np.array_equal(got[r], want[0])
 
 
 @pytest.mark.parametrize("kind_name,w", [("ADD_MAJ", 32), ("ADD_NW", 8), ("MUL_TREE", 8),

@@ -1,8 +1,10 @@
 """Serving (continuous batching) through the C ABI: requests of mixed kinds
 and widths submitted while others run; every result is bit-identical to the
 same request run alone and to the oracle (n = 16 ring-size-1024 parameters
-so the oracle is quick), and a pool budget smaller than the mix forces
-requests to wait for rows without changing any result."""
+so the oracle is quick, and a mix of every served kind at full parameters,
+n = 500), and a pool budget smaller than the mix forces requests to wait
+for rows without changing any result."""
+import concurrent.futures as cf
 import threading
 import time
 
@@ -70,10 +72,12 @@ def _oracle(env, req):
     return orc.matvec(P, bk, ksk, w, h0, h1)[0]
 
 
-def _serve(env, reqs, budget, max_batch=0, spacing_s=0.0, threads=1):
+def _serve(env, reqs, budget, max_batch=0, spacing_s=0.0, threads=1, free_hbm=0):
     torch, api, p = env["torch"], env["api"], env["p"]
     ctx = api.Context(p)
     ctx.set_keys(env["bk"], env["ksk"])
+    if free_hbm:
+        ctx.set_option(api.OPT_TEST_FREE_HBM, free_hbm)
     outs = [torch.zeros(req[8] + (api.LWE_STRIDE,), dtype=torch.int32, device="cuda") for req in reqs]
     torch.cuda.synchronize()
     ctx.serve_start(budget, max_batch)
@@ -125,6 +129,43 @@ def test_small_pool_forces_queueing(env):
         assert np.array_equal(a, b)
 
 
+def _mul16_requests(env, seed, count):
+    api, p, P, kd, orc = env["api"], env["p"], env["P"], env["kd"], __import__("oracle")
+    d = api.to_device
+    s_dev = d(kd.s)
+    reqs = []
+    for k in range(count):
+        bits = [synth.random_bits((16,), seed * 100 + k, f"gm{j}") for j in range(2)]
+        cds = [synth.ct_draws(p, b.shape, seed * 100 + k, f"gm{j}") for j, b in enumerate(bits)]
+        dev = [api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(b)) for cd, b in zip(cds, bits)]
+        host = [orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, b) for cd, b in zip(cds, bits)]
+        reqs.append((api.MUL, 16, 0, 0, dev[0], dev[1], host[0], host[1], (16,)))
+    return reqs
+
+
+def test_pool_grows_from_free_hbm_and_waits_when_short(env):
+    """Admission by free device memory.  Twelve 16-bit multiplications (680
+    pool rows of 2 KB each) submitted at once outgrow the pool's first 8 MB:
+    the pool maps more device memory and admits them while others run.
+    With the device's free memory reported as 1 byte (test hook), the pool
+    cannot grow, so requests wait for the rows of finished ones; every
+    result is the same either way, and equal to the oracle's."""
+    reqs = _mul16_requests(env, 7, 12)
+    grown, _, st_g = _serve(env, reqs, budget=1 << 30)
+    assert st_g["completed"] == len(reqs) and st_g["failed"] == 0
+    assert st_g["pool_grows"] >= 1 and st_g["pool_bytes"] > (8 << 20)
+    assert st_g["pool_cap_bytes"] >= (1 << 30)
+    assert st_g["admitted_busy"] >= 1
+    short, _, st_s = _serve(env, reqs, budget=1 << 30, free_hbm=1)
+    assert st_s["completed"] == len(reqs) and st_s["failed"] == 0
+    assert st_s["pool_grows"] == 0 and st_s["pool_bytes"] < st_g["pool_bytes"]
+    for a, b in zip(grown, short):
+        assert np.array_equal(a, b)
+    for k in (0, 11):
+        want = _oracle(env, reqs[k])
+        assert np.array_equal(grown[k], want)
+
+
 def test_wait_timeout_then_result(env):
     """A client wait that runs out is reported, not hung: waiting 1 ms on a
     16-bit multiplication (56 levels, well over 1 ms) raises TFHE_ETIMEOUT;
@@ -154,3 +195,68 @@ def test_wait_timeout_then_result(env):
         assert np.array_equal(got, want[0])
     finally:
         ctx.close()
+
+
+@pytest.fixture(scope="module")
+def full_env(orc):
+    """Full parameters (n = 500), keys from the master seed."""
+    import torch
+    from paper_2005_01945_gb300 import api, build
+    build.build()
+    p = synth.TFHEParams()
+    P = oparams(p)
+    kd = synth.key_draws(p, synth.MASTER_SEED)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    obk = orc.keygen_bk(P, kd.s, kd.S, kd.bk_mask, kd.bk_noise)
+    oksk = orc.keygen_ksk(P, kd.s, kd.S, kd.ksk_mask, kd.ksk_noise)
+    yield dict(torch=torch, api=api, p=p, P=P, kd=kd, bk=bk, ksk=ksk, obk=obk, oksk=oksk)
+
+
+def _full_requests(env, seed):
+    """One request of every kind the served workload draws from (single gate,
+    16- and 32-bit addition, 16- and 32-bit multiplication), plus a second
+    gate and 16-bit addition, on uniform random operands."""
+    api, p, P, kd, orc = env["api"], env["p"], env["P"], env["kd"], __import__("oracle")
+    d = api.to_device
+    s_dev = d(kd.s)
+    kinds = [(api.GATE, api.XOR), (api.ADD, 16), (api.MUL, 32), (api.ADD, 32), (api.MUL, 16),
+             (api.GATE, api.AND), (api.ADD, 16)]
+    reqs = []
+    for k, (kind, w) in enumerate(kinds):
+        nb = 1 if kind == api.GATE else w
+        bits = [synth.random_bits((nb,), seed * 100 + k, f"fin{j}") for j in range(2)]
+        cds = [synth.ct_draws(p, b.shape, seed * 100 + k, f"fin{j}") for j, b in enumerate(bits)]
+        dev = [api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(b)) for cd, b in zip(cds, bits)]
+        host = [orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, b) for cd, b in zip(cds, bits)]
+        reqs.append((kind, w, 0, 0, dev[0], dev[1], host[0], host[1], (nb,)))
+    return reqs
+
+
+def test_full_parameters_mix_equals_alone_and_oracle(full_env):
+    """Served mix at full parameters (n = 500): requests of every kind are
+    submitted from three threads while others run, so they share levels on
+    the device.  Each result equals the same request served alone; the
+    gates, additions and the 16-bit multiplication equal the oracle's
+    ciphertexts word for word (recomputed gate by gate, up to 62 levels
+    deep), and the 32-bit multiplication decrypts to the product."""
+    env = full_env
+    api, orc = env["api"], __import__("oracle")
+    reqs = _full_requests(env, 17)
+    mixed, lat, stats = _serve(env, reqs, budget=512 << 20, spacing_s=0.003, threads=3)
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert all(x > 0 for x in lat)
+    alone = [_serve(env, [req], budget=128 << 20)[0][0] for req in reqs]
+    for k in range(len(reqs)):
+        assert np.array_equal(mixed[k], alone[k]), k
+    checked = [k for k, r in enumerate(reqs) if not (r[0] == api.MUL and r[1] == 32)]
+    with cf.ThreadPoolExecutor(len(checked)) as ex:
+        wants = list(ex.map(lambda k: _oracle(env, reqs[k]), checked))
+    for k, want in zip(checked, wants):
+        assert np.array_equal(mixed[k].reshape(want.shape), want), k
+    k32 = next(k for k, r in enumerate(reqs) if r[0] == api.MUL and r[1] == 32)
+    bits = orc.decrypt_bits(env["P"], env["kd"].s, mixed[k32])
+    a = synth.from_bits(orc.decrypt_bits(env["P"], env["kd"].s, reqs[k32][6])[None])[0]
+    b = synth.from_bits(orc.decrypt_bits(env["P"], env["kd"].s, reqs[k32][7])[None])[0]
+    assert synth.from_bits(bits[None])[0] == (int(a) * int(b)) % (1 << 32)
