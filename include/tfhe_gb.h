@@ -307,8 +307,14 @@ typedef enum {
     TFHE_OPT_BR_GROUP = 3,   /* blind-rotation CTA shape: 1, 2 or 4 bootstraps per  */
                              /*    CTA (4 warps each), 8 = one bootstrap on 8 warps, */
                              /*    16 = one bootstrap on a cluster of two CTAs (two */
-                             /*    SMs, one prime each; lowest latency), or 0       */
-                             /*    (default): autotuned, else by batch size         */
+                             /*    SMs, one prime each; lowest latency), 32 = two   */
+                             /*    bootstraps per CTA with each CMux step's key     */
+                             /*    staged in shared memory by bulk copies (one CTA  */
+                             /*    per SM), 33 = the same shape and occupancy with  */
+                             /*    the key read through L1 (the staging's control), */
+                             /*    40 = one bootstrap on 8 warps with the key       */
+                             /*    staged, or 0 (default): autotuned, else by       */
+                             /*    batch size                                       */
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
     TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave,   */
                              /*    4 bootstraps per SM)                             */

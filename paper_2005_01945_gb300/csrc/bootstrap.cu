@@ -382,6 +382,62 @@ struct BrSmem {                 // one bootstrap
     uint16_t abar[kLweStride];  // mod-switched mask and body
 };
 
+// Bootstrapping key staged in shared memory (shape kBrStaged): the key of
+// CMux step i + 1, 64 KB, is bulk-copied (the TMA engine's cp.async.bulk,
+// completion counted on an mbarrier) into one buffer while step i reads the
+// other; the pointwise phase then reads the key from shared memory instead
+// of through L1.
+struct BkStage {
+    uint4 bk[2][4][kN];         // [buffer][poly p * 2 + prime h][reg*32+lane]
+    unsigned long long full[2]; // buffer landed
+    uint32_t issued[2];         // uses issued into each buffer
+    volatile int abort;         // a wait ran out: read the key from global memory
+};
+constexpr uint32_t kBkStepBytes = 4 * kN * sizeof(uint4);   // 64 KB
+constexpr long kBkSpin = 1L << 20;                           // x ~1 us per try
+
+__device__ __forceinline__ uint32_t br_saddr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bounded wait for phase `parity` of a stage barrier; false if it ran out.
+__device__ __forceinline__ bool bk_wait(unsigned long long *bar, uint32_t parity)
+{
+    for (long i = 0; i < kBkSpin; ++i) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(br_saddr(bar)), "r"(parity), "r"(1000u)
+                     : "memory");
+        if (ok)
+            return true;
+    }
+    return false;
+}
+
+// One thread: queue the key of CMux step i into buffer `buf` (four 16 KB
+// bulk copies of the step's contiguous 64 KB).
+__device__ __forceinline__ void bk_issue(BkStage &G, const uint4 *bk_ntt, int i, int buf)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     br_saddr(&G.full[buf])),
+                 "r"(kBkStepBytes)
+                 : "memory");
+    const uint4 *src = bk_ntt + (long)i * 4 * kN;
+#pragma unroll
+    for (int part = 0; part < 4; ++part)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                     "[%0], [%1], %2, [%3];" ::"r"(br_saddr(&G.bk[buf][part][0])),
+                     "l"(src + part * kN), "r"((uint32_t)(kN * sizeof(uint4))),
+                     "r"(br_saddr(&G.full[buf]))
+                     : "memory");
+    G.issued[buf]++;
+}
+
 // Phase 1: warp (c, h) forms both digit polynomials of TLWE polynomial c of
 // X^a acc - acc (one rotation, two digit extractions) and transforms them
 // modulo prime h; results go to S.fwd[2c + j][h].  One transform copy: the
@@ -462,6 +518,29 @@ __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
     for (int r = 0; r < 32; ++r) {
         const uint4 b = __ldg(bkp + r * 32 + lane);
         const int e = r * 32 + lane;
+        uint64_t s = (uint64_t)f0[e] * b.x;
+        s += (uint64_t)f1[e] * b.y;
+        s += (uint64_t)f2[e] * b.z;
+        s += (uint64_t)f3[e] * b.w;
+        x[r] = mont_reduce(s, pr.q, qn);
+    }
+}
+
+// Phase 2 with the key staged in shared memory (shape kBrStaged).
+__device__ __forceinline__ void br_pointwise_staged(uint32_t (&x)[32], const BrSmem &S,
+                                                    const uint4 *bks, int lane, const Prime &pr)
+{
+    const uint32_t qn = c_ntt.q_inv[pr.P];
+    const uint32_t *f0 = S.fwd[0][pr.P], *f1 = S.fwd[1][pr.P], *f2 = S.fwd[2][pr.P],
+                   *f3 = S.fwd[3][pr.P];
+    const uint32_t base = br_saddr(bks);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int e = r * 32 + lane;
+        uint4 b;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                     : "r"(base + (uint32_t)e * 16u));
         uint64_t s = (uint64_t)f0[e] * b.x;
         s += (uint64_t)f1[e] * b.y;
         s += (uint64_t)f2[e] * b.z;
@@ -629,7 +708,7 @@ __device__ __forceinline__ void br_extract(const BrArgs &A, long g, const uint32
 //   W = 8: warp (c, j, h) runs phase 1 for digit j of polynomial c; warps
 //          0..3 run phases 2-3 as (p, h); every warp runs phase 4 on a
 //          quarter of polynomial w >> 2.
-template <int B, int W>
+template <int B, int W, int STAGE = 0>
 __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 / (W * B))
     k_blind_rotate(const BrArgs A)
 {
@@ -638,14 +717,31 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bi = warp / W, wr = warp % W, tb = tid % T;   // bootstrap slot, role
     BrSmem &S = reinterpret_cast<BrSmem *>(smem_raw)[bi];
+    BkStage &G = *reinterpret_cast<BkStage *>(reinterpret_cast<BrSmem *>(smem_raw) + B);
     const int lane_brv = brv5(lane);
     const int n = A.keys.n;
     const int w4 = wr & 3, p = w4 >> 1, h = wr & 1;
     const Prime pr((uint32_t)h);
+    uint32_t uses = 0;   // staged steps so far (the same in every thread)
+
+    if (STAGE) {
+        if (tid == 0) {
+            for (int b = 0; b < 2; ++b) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(br_saddr(&G.full[b]))
+                             : "memory");
+                G.issued[b] = 0;
+            }
+            G.abort = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
 
     for (long grp = blockIdx.x; grp * B < A.count; grp += gridDim.x) {
         const long g = grp * B + bi;
         const bool active = br_prologue<T>(A, g, tb, S.abar, true);
+        if (STAGE && tid == 0 && n > 0 && !G.abort)
+            bk_issue(G, A.keys.bk_ntt, 0, uses & 1);
         __syncthreads();
         br_acc_init<T>(A, S.acc, S.abar[n], tb);
         __syncthreads();
@@ -653,19 +749,45 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
         // ---- n CMux steps, all B bootstraps in lockstep
         const BrSmem *all = reinterpret_cast<const BrSmem *>(smem_raw);
         for (int i = 0; i < n; ++i) {
+            const uint32_t u = uses;   // this step's use of buffer u & 1
+            if (STAGE) {
+                ++uses;
+                // the other buffer was last read in step i - 1, before the
+                // barrier that ended that step's pointwise phase
+                if (tid == 0 && i + 1 < n && !G.abort)
+                    bk_issue(G, A.keys.bk_ntt, i + 1, (u + 1) & 1);
+            }
             int any = 0;
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 any |= all[b].abar[i];
-            if (any == 0)
-                continue;  // X^0 acc - acc = 0 for every slot: nothing changes
+            if (any == 0) {
+                // X^0 acc - acc = 0 for every slot: nothing changes; the
+                // step's copy still has to land before its buffer is reused
+                if (STAGE && tid == 0 && !G.abort && !bk_wait(&G.full[u & 1], (u >> 1) & 1)) {
+                    G.abort = 1;
+                    atomicOr(A.status, kErrTimeout);
+                }
+                continue;
+            }
             const int a = S.abar[i];  // a = 0 here gives zero digits: acc unchanged
             uint32_t x[32];
             const uint4 *bki = A.keys.bk_ntt + (((long)i * 2 + p) * 2 + h) * 1024;
             if (W == 4) {
                 br_digits_fwd(x, S, p, a, lane, A.keys.twb, pr);
                 __syncthreads();
-                br_pointwise(x, S, bki, lane, pr);
+                bool staged = false;
+                if (STAGE) {
+                    staged = !G.abort && bk_wait(&G.full[u & 1], (u >> 1) & 1);
+                    if (!staged && !G.abort) {
+                        G.abort = 1;   // read this and later steps from global memory
+                        atomicOr(A.status, kErrTimeout);
+                    }
+                }
+                if (staged)
+                    br_pointwise_staged(x, S, &G.bk[u & 1][p * 2 + h][0], lane, pr);
+                else
+                    br_pointwise(x, S, bki, lane, pr);
                 __syncthreads();
                 br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
                 __syncthreads();
@@ -674,8 +796,20 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
             } else {
                 br_digit_fwd(x, S, wr >> 2, (wr >> 1) & 1, a, lane, A.keys.twb, pr);
                 __syncthreads();
-                if (wr < 4)
-                    br_pointwise(x, S, bki, lane, pr);
+                if (wr < 4) {
+                    bool staged = false;
+                    if (STAGE) {
+                        staged = !G.abort && bk_wait(&G.full[u & 1], (u >> 1) & 1);
+                        if (!staged && !G.abort) {
+                            G.abort = 1;   // read this and later steps from global memory
+                            atomicOr(A.status, kErrTimeout);
+                        }
+                    }
+                    if (staged)
+                        br_pointwise_staged(x, S, &G.bk[u & 1][p * 2 + h][0], lane, pr);
+                    else
+                        br_pointwise(x, S, bki, lane, pr);
+                }
                 __syncthreads();
                 if (wr < 4)
                     br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
@@ -689,6 +823,12 @@ __global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 /
             br_extract<T>(A, g, S.acc, tb);
         __syncthreads();
     }
+    // after a wait that ran out: copies still in flight land before the
+    // CTA's shared memory is released (the last use of each buffer)
+    if (STAGE && tid == 0 && G.abort)
+        for (int b = 0; b < 2; ++b)
+            if (G.issued[b])
+                (void)bk_wait(&G.full[b], (G.issued[b] - 1) & 1);
 }
 
 // ---------------------------------------------------------------------
@@ -909,33 +1049,45 @@ cudaError_t launch_bk_to_ntt(const int32_t *bk_dev, uint32_t *bk_ntt, int n, con
     return cudaGetLastError();
 }
 
-template <int B, int W>
-static void br_prepare()
+// Dynamic shared memory of a shape: B bootstraps, plus the key stages for
+// the staged shape and its control (which reserves them unused, so both run
+// one CTA per SM).
+template <int B, int STAGE>
+constexpr size_t br_smem(bool stage_room)
 {
-    cudaFuncSetAttribute(k_blind_rotate<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(B * sizeof(BrSmem)));
-    cudaFuncSetAttribute(k_blind_rotate<B, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return B * sizeof(BrSmem) + (STAGE || stage_room ? sizeof(BkStage) : 0);
+}
+
+template <int B, int W, int STAGE = 0>
+static void br_prepare(size_t smem)
+{
+    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     (void)cudaGetLastError();
 }
 
-template <int B, int W>
-static int br_blocks(int dev)
+template <int B, int W, int STAGE = 0>
+static int br_blocks(int dev, bool stage_room = false)
 {
-    static int cached[64] = {0};
+    static int cached[2][64] = {{0}};
     if (dev < 0 || dev >= 64)
         return 1;
-    if (!cached[dev]) {
-        br_prepare<B, W>();
+    const size_t smem = br_smem<B, STAGE>(stage_room);
+    if (!cached[stage_room][dev]) {
+        // the attribute covers the larger of the two requests of the shape
+        br_prepare<B, W, STAGE>(br_smem<B, STAGE>(B == 2 && W == 4));
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W>, 32 * W * B,
-                                                          B * sizeof(BrSmem)) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W, STAGE>,
+                                                          32 * W * B, smem) != cudaSuccess) {
             (void)cudaGetLastError();
             nb = 0;
         }
-        cached[dev] = nb > 0 ? nb : 1;
+        cached[stage_room][dev] = nb > 0 ? nb : 1;
     }
-    return cached[dev];
+    return cached[stage_room][dev];
 }
 
 // Bootstraps in flight per SM for the variant (all variants: 16 warps).
@@ -955,7 +1107,8 @@ int br_blocks_per_sm()
 // per CMux, for levels narrower than the GPU).
 static bool br_shape_ok(int v)
 {
-    return v == 1 || v == 2 || v == 4 || v == kBrSplit || v == kBrPair;
+    return v == 1 || v == 2 || v == 4 || v == kBrSplit || v == kBrPair || v == kBrStaged ||
+           v == kBrStagedCtl || v == kBrSplitStaged;
 }
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
@@ -1022,10 +1175,14 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_blind_rotate_pair, A);
     }
-    const int B = shape == kBrSplit ? 1 : shape;
+    const int B = (shape == kBrSplit || shape == kBrSplitStaged) ? 1
+                : (shape == kBrStaged || shape == kBrStagedCtl) ? 2 : shape;
     const long groups = (count + B - 1) / B;
     long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)
                        : shape == 2 ? br_blocks<2, 4>(dev)
+                       : shape == kBrStaged ? br_blocks<2, 4, 1>(dev)
+                       : shape == kBrStagedCtl ? br_blocks<2, 4>(dev, true)
+                       : shape == kBrSplitStaged ? br_blocks<1, 8, 1>(dev)
                        : shape == kBrSplit ? br_blocks<1, 8>(dev) : br_blocks<1, 4>(dev);
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
     const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
@@ -1033,6 +1190,15 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     switch (shape) {
     case 4: k_blind_rotate<4, 4><<<blocks, 512, 4 * sizeof(BrSmem), stream>>>(A); break;
     case 2: k_blind_rotate<2, 4><<<blocks, 256, 2 * sizeof(BrSmem), stream>>>(A); break;
+    case kBrStaged:
+        k_blind_rotate<2, 4, 1><<<blocks, 256, br_smem<2, 1>(false), stream>>>(A);
+        break;
+    case kBrStagedCtl:
+        k_blind_rotate<2, 4><<<blocks, 256, br_smem<2, 0>(true), stream>>>(A);
+        break;
+    case kBrSplitStaged:
+        k_blind_rotate<1, 8, 1><<<blocks, 256, br_smem<1, 1>(false), stream>>>(A);
+        break;
     case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
     default: k_blind_rotate<1, 4><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
     }

@@ -1260,8 +1260,9 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
         return TFHE_OK;
     case TFHE_OPT_BR_GROUP:
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != kBrSplit &&
-            value != kBrPair)
-            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 8 or 16");
+            value != kBrPair && value != kBrStaged && value != kBrStagedCtl &&
+            value != kBrSplitStaged)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 8, 16, 32, 33 or 40");
         ctx->keys.br_group = (int)value;
         invalidate_graphs(ctx);   // captured graphs hold the old launch shape
         return TFHE_OK;

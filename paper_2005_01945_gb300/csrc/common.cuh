@@ -75,6 +75,14 @@ __device__ __forceinline__ uint32_t mont_reduce(uint64_t x, uint32_t q, uint32_t
 // codes, 1, 2 and 4, count 4-warp bootstraps per CTA.
 constexpr int kBrSplit = 8;
 constexpr int kBrPair = 16;
+// Two 4-warp bootstraps per CTA with the CMux step's key staged in shared
+// memory by bulk copies (one CTA per SM), and, for measuring that choice,
+// the same shape reading the key through L1 at the same occupancy.
+constexpr int kBrStaged = 32;
+constexpr int kBrStagedCtl = 33;
+// One bootstrap on 8 warps with the key staged (the latency shape, whose
+// single pointwise warp per sub-partition otherwise waits on L2 each step).
+constexpr int kBrSplitStaged = 40;
 // Key-switch launch code for the tiled kernel (shared-memory key stages);
 // the codes 1 .. 32 are j-chunks of the direct kernel.
 constexpr int kKsTiled = 64;

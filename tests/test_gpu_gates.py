@@ -275,12 +275,15 @@ def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
     assert np.array_equal(got[sample, :p.n + 1], want)
 
 
-@pytest.mark.parametrize("group", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("group", [1, 2, 4, 8, 16, 32, 33, 40])
 def test_each_lockstep_group_bit_exact(gpu, orc, group):
     """Blind rotation with 1, 2 or 4 bootstraps per CTA (13 gates leave empty
     slots in the last group, and skipped CMux steps in some slots), with one
-    bootstrap spread over 8 warps (shape 8), and with one bootstrap on a
-    cluster of two CTAs exchanging residues (shape 16)."""
+    bootstrap spread over 8 warps (shape 8), with one bootstrap on a
+    cluster of two CTAs exchanging residues (shape 16), and with two per
+    CTA reading the key from bulk-copied shared-memory stages (shape 32) or,
+    at the same occupancy, through L1 (shape 33), and one bootstrap on 8
+    warps with the key staged (shape 40)."""
     torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
     count = 13
     bits, cts, dev = _fresh(gpu, orc, count, 40 + group, f"grp{group}", zero_some=True)
@@ -293,6 +296,31 @@ def test_each_lockstep_group_bit_exact(gpu, orc, group):
         gpu["ctx"].set_option(api.OPT_BR_GROUP, 0)
     want = orc.gates(P, gpu["obk"], gpu["oksk"], ops, cts[0], cts[1])
     assert np.array_equal(_u32(out)[:, :p.n + 1], want)
+
+
+def test_staged_key_across_groups(gpu, orc):
+    """The key-staging shape on 700 gates: most CTAs run two or more groups
+    of two bootstraps, so the staged buffers and their barriers carry over
+    from group to group.  Every output equals the default shape's, and
+    sampled ones the oracle's."""
+    torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
+    count = 700
+    bits, cts, dev = _fresh(gpu, orc, count, 91, "stg")
+    ops = ((np.arange(count) * 3) % 6).astype(np.uint8)
+    ref = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    got = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
+    gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], ref)
+    gpu["ctx"].set_option(api.OPT_BR_GROUP, 32)
+    try:
+        gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], got)
+    finally:
+        gpu["ctx"].set_option(api.OPT_BR_GROUP, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert gpu["ctx"].status() == 0
+    idx = np.array([0, 303, 304, 305, 699])
+    want = orc.gates(P, gpu["obk"], gpu["oksk"], ops[idx], cts[0][idx], cts[1][idx])
+    assert np.array_equal(_u32(got)[idx, :p.n + 1], want)
 
 
 def test_autotune_keeps_results(gpu, orc):
