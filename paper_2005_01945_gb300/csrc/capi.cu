@@ -89,10 +89,15 @@ int run_bootstrap(tfhe_ctx *ctx, const uint8_t *ops, const int32_t *a, const int
     int rc = ensure_big(ctx, (size_t)count);
     if (rc != TFHE_OK)
         return rc;
-    cudaError_t e = launch_blind_rotate(ctx->keys, ops, a, idx_a, rows_a, b, idx_b, rows_b,
-                                        ctx->big, count, mu, ctx->status, ctx->br_grid, stream);
+    cudaError_t e;
+    {
+        NvtxRange r("tfhe: gate combine + mod switch + blind rotation + extraction");
+        e = launch_blind_rotate(ctx->keys, ops, a, idx_a, rows_a, b, idx_b, rows_b, ctx->big,
+                                count, mu, ctx->status, ctx->br_grid, stream);
+    }
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "blind rotation launch");
+    NvtxRange r("tfhe: key switch");
     e = launch_keyswitch(ctx->keys.ksk, ctx->big, out, idx_out, rows_out, count, ctx->prm.n,
                          ctx->num_sms, ctx->status, stream, &ctx->keys);
     if (e != cudaSuccess)

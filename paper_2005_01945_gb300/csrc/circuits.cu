@@ -993,6 +993,7 @@ static cudaError_t enqueue_per_gate(tfhe_ctx *ctx, Plan &P, cudaStream_t st)
 
 static int run_plan(tfhe_ctx *ctx, Plan &P, const tfhe_job *jobs, cudaStream_t st)
 {
+    NvtxRange range("tfhe: circuit schedule (levels of blind rotation + key switch)");
     CircuitCache &C = cache_of(ctx);
     cudaError_t e = cudaSuccess;
     // inputs -> pool (strided 2D copies, one per input group)

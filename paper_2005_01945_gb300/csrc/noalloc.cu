@@ -122,6 +122,7 @@ extern "C" int tfhe_bootstrap_gates_noalloc(tfhe_ctx *ctx, const uint8_t *ops, c
         return rc;
     const long n = (long)count;
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxRange range("tfhe: gate bootstrapping (fixed scratch)");
     cudaError_t e = launch_blind_rotate(ctx->keys, ops, a, nullptr, n, b, nullptr, n, big, n, kMu,
                                         ctx->status, ctx->br_grid, st);
     if (e != cudaSuccess)

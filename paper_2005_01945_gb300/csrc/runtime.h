@@ -2,6 +2,8 @@
 #pragma once
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace tgb {
@@ -45,6 +47,15 @@ struct DeviceGuard {
         if (prev >= 0)
             cudaSetDevice(prev);
     }
+};
+
+// A named range on the host timeline of profilers (NVTX; costs a pointer
+// check when no profiler is attached): one per phase a call enqueues.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 int fail(tfhe_ctx *ctx, int code, const char *fmt, ...);
