@@ -935,6 +935,8 @@ def main():
             configs[name] = {"workload": desc, "gates_per_step": gates,
                              "steps": len(ms), "warmup": 1, "ms_per_step": float(np.mean(ms)),
                              "gates_per_s": gates * len(ms) / (sum(ms) / 1e3),
+                             "levels_per_step": cbl // max(len(ms), 1),
+                             "bootstraps_per_launch": cbb / max(cbl, 1),
                              "roofline": {k: rl[k] for k in ("kernel", "bound", "achieved",
                                                              "peak", "unit", "frac",
                                                              "avg_launch_ms", "launches",

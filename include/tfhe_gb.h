@@ -305,7 +305,8 @@ typedef enum {
                              /*    and key-switch launch of circuit schedules (also */
                              /*    inside captured graphs)                          */
     TFHE_OPT_BR_GROUP = 3,   /* blind-rotation CTA shape: 1, 2 or 4 bootstraps per  */
-                             /*    CTA (4 warps each), 8 = one bootstrap on 8 warps, */
+                             /*    CTA (4 warps each), 5 = one per 4-warp CTA at 5  */
+                             /*    CTAs per SM, 8 = one bootstrap on 8 warps,       */
                              /*    16 = one bootstrap on a cluster of two CTAs (two */
                              /*    SMs, one prime each; lowest latency), 32 = two   */
                              /*    bootstraps per CTA with each CMux step's key     */
@@ -316,8 +317,10 @@ typedef enum {
                              /*    staged, or 0 (default): autotuned, else by       */
                              /*    batch size                                       */
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
-    TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave,   */
-                             /*    4 bootstraps per SM)                             */
+    TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave    */
+                             /*    of 4 bootstraps per SM, or of 5 per SM (shape 5) */
+                             /*    where the autotuner's wave times make that       */
+                             /*    schedule cheaper)                                */
     TFHE_OPT_KS_KERNEL = 6,  /* key-switch kernel: 64 = tiled (64 gates per CTA, key */
                              /*    rows staged in shared memory by bulk copies),    */
                              /*    1, 2, 4, .. 32 = direct kernel with that j-split, */
@@ -340,8 +343,10 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value);
  * context's device: for each level-width bucket (<= 152, 304, 608, 1216,
  * 2432, 4864, 9728 gates, and more) time the blind-rotation CTA shapes
  * (TFHE_OPT_BR_GROUP values) and the key-switch kernels (TFHE_OPT_KS_KERNEL
- * values) on synthetic ciphertexts, and keep the fastest (a few seconds;
- * results never change).  cache_path (may be NULL): a text file consulted
+ * values) on synthetic ciphertexts, and keep the fastest; then time one
+ * full wave of 4 bootstraps per SM and one of 5 per SM, from which each
+ * circuit schedule picks its wave size (a few seconds; results never
+ * change).  cache_path (may be NULL): a text file consulted
  * first and appended to after tuning, keyed by device name and SM count.
  * choices (may be NULL) receives 16 ints: the 8 blind-rotation shapes, then
  * the 8 key-switch choices.  Synchronous. */

@@ -708,8 +708,9 @@ __device__ __forceinline__ void br_extract(const BrArgs &A, long g, const uint32
 //   W = 8: warp (c, j, h) runs phase 1 for digit j of polynomial c; warps
 //          0..3 run phases 2-3 as (p, h); every warp runs phase 4 on a
 //          quarter of polynomial w >> 2.
-template <int B, int W, int STAGE = 0>
-__global__ void __launch_bounds__(32 * W * B, (W * B >= 16 || W == 8) ? 1 : 16 / (W * B))
+template <int B, int W, int STAGE = 0, int MINB = 0>
+__global__ void __launch_bounds__(32 * W * B,
+                                  MINB ? MINB : ((W * B >= 16 || W == 8) ? 1 : 16 / (W * B)))
     k_blind_rotate(const BrArgs A)
 {
     constexpr int T = 32 * W;      // threads per bootstrap
@@ -1058,18 +1059,18 @@ constexpr size_t br_smem(bool stage_room)
     return B * sizeof(BrSmem) + (STAGE || stage_room ? sizeof(BkStage) : 0);
 }
 
-template <int B, int W, int STAGE = 0>
+template <int B, int W, int STAGE = 0, int MINB = 0>
 static void br_prepare(size_t smem)
 {
-    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE>,
+    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE, MINB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_blind_rotate<B, W, STAGE, MINB>,
                          cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     (void)cudaGetLastError();
 }
 
-template <int B, int W, int STAGE = 0>
+template <int B, int W, int STAGE = 0, int MINB = 0>
 static int br_blocks(int dev, bool stage_room = false)
 {
     static int cached[2][64] = {{0}};
@@ -1078,9 +1079,9 @@ static int br_blocks(int dev, bool stage_room = false)
     const size_t smem = br_smem<B, STAGE>(stage_room);
     if (!cached[stage_room][dev]) {
         // the attribute covers the larger of the two requests of the shape
-        br_prepare<B, W, STAGE>(br_smem<B, STAGE>(B == 2 && W == 4));
+        br_prepare<B, W, STAGE, MINB>(br_smem<B, STAGE>(B == 2 && W == 4));
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W, STAGE>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W, STAGE, MINB>,
                                                           32 * W * B, smem) != cudaSuccess) {
             (void)cudaGetLastError();
             nb = 0;
@@ -1108,7 +1109,7 @@ int br_blocks_per_sm()
 static bool br_shape_ok(int v)
 {
     return v == 1 || v == 2 || v == 4 || v == kBrSplit || v == kBrPair || v == kBrStaged ||
-           v == kBrStagedCtl || v == kBrSplitStaged;
+           v == kBrStagedCtl || v == kBrSplitStaged || v == kBrFive;
 }
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
@@ -1175,7 +1176,7 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_blind_rotate_pair, A);
     }
-    const int B = (shape == kBrSplit || shape == kBrSplitStaged) ? 1
+    const int B = (shape == kBrSplit || shape == kBrSplitStaged || shape == kBrFive) ? 1
                 : (shape == kBrStaged || shape == kBrStagedCtl) ? 2 : shape;
     const long groups = (count + B - 1) / B;
     long blocks_per_sm = shape == 4 ? br_blocks<4, 4>(dev)
@@ -1183,6 +1184,7 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
                        : shape == kBrStaged ? br_blocks<2, 4, 1>(dev)
                        : shape == kBrStagedCtl ? br_blocks<2, 4>(dev, true)
                        : shape == kBrSplitStaged ? br_blocks<1, 8, 1>(dev)
+                       : shape == kBrFive ? br_blocks<1, 4, 0, 5>(dev)
                        : shape == kBrSplit ? br_blocks<1, 8>(dev) : br_blocks<1, 4>(dev);
     const long cap = blocks_per_sm * (sms > 0 ? sms : 1);
     const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
@@ -1199,6 +1201,7 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     case kBrSplitStaged:
         k_blind_rotate<1, 8, 1><<<blocks, 256, br_smem<1, 1>(false), stream>>>(A);
         break;
+    case kBrFive: k_blind_rotate<1, 4, 0, 5><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
     case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
     default: k_blind_rotate<1, 4><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
     }

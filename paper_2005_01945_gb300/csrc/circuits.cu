@@ -590,6 +590,8 @@ struct Plan {
     bool graph_failed = false;
     bool graph_profiled = false;     // graph carries event-record nodes
     long kernels_per_run = 0;        // kernel launches of one level sequence
+    long wave = 0;                   // gates per level unit the schedule rounds to
+    int wide_shape = 0;              // blind-rotation shape of levels of >= wave gates
     std::vector<cudaEvent_t> ev;     // 3 per level: BR start, BR end / KS start, KS end
 
     ~Plan()
@@ -616,7 +618,8 @@ struct CircuitCache {
     bool per_gate = false;
     bool profile = false;
     int policy = TFHE_SCHED_BALANCED;
-    long level_width = 0;            // 0: one wave (4 bootstraps per SM)
+    long level_width = 0;            // 0: one wave, of 4 or 5 bootstraps per SM
+    std::map<std::string, long> wave_choice;   // job signature -> chosen wave
     std::vector<Plan *> profiled;    // plans whose events hold the last run
     cudaStream_t capture_stream = nullptr;
     ~CircuitCache()
@@ -638,6 +641,7 @@ void invalidate_graphs(tfhe_ctx *ctx)
 {
     if (!ctx->circuits)
         return;
+    ctx->circuits->wave_choice.clear();   // wave times may have changed
     for (auto &kv : ctx->circuits->plans)
         if (kv.second->graph) {
             cudaGraphExecDestroy(kv.second->graph);
@@ -951,8 +955,11 @@ static cudaError_t enqueue_levels(tfhe_ctx *ctx, Plan &P, cudaStream_t st, bool 
         if (cnt == 0)
             continue;
         cudaError_t e = mark(3 * (l - 1));
+        DevKeys K = ctx->keys;
+        if (P.wide_shape && K.br_group == 0 && cnt >= P.wave)
+            K.br_group = P.wide_shape;
         if (e == cudaSuccess)
-            e = launch_blind_rotate(ctx->keys, P.d_ops + off, P.pool, P.d_ia + off, P.pool_rows,
+            e = launch_blind_rotate(K, P.d_ops + off, P.pool, P.d_ia + off, P.pool_rows,
                                     P.pool, P.d_ib + off, P.pool_rows, P.big, cnt, kMu,
                                     ctx->status, ctx->br_grid, st, P.d_ic ? P.pool : nullptr,
                                     P.d_ic ? P.d_ic + off : nullptr, P.pool_rows);
@@ -1071,6 +1078,38 @@ static int run_plan(tfhe_ctx *ctx, Plan &P, const tfhe_job *jobs, cudaStream_t s
     return TFHE_OK;
 }
 
+// Wave size of a job mix's level schedule: 4 bootstraps per SM (the tuned
+// shapes) or 5 (kBrFive, 20 warps per SM).  Each level of a schedule built
+// for wave W costs about ceil(width / W) full waves; with the autotuner's
+// time of one full wave of each kind, the schedule with the lower total is
+// used, once it is at least 1 % cheaper.  Decided once per job mix.
+static long choose_wave(tfhe_ctx *ctx, CircuitCache &C, const std::string &sig,
+                        const tfhe_job *jobs, size_t njobs)
+{
+    const long w4 = 4L * ctx->num_sms, w5 = 5L * ctx->num_sms;
+    const float t4 = ctx->keys.wave_ms[0], t5 = ctx->keys.wave_ms[1];
+    if (!(t4 > 0.f && t5 > 0.f) || t5 / w5 >= 0.99f * t4 / w4)
+        return w4;
+    auto it = C.wave_choice.find(sig);
+    if (it != C.wave_choice.end())
+        return it->second;
+    auto cost = [&](long w, float t) -> double {
+        Schedule S;
+        if (build_schedule(nullptr, jobs, njobs, TFHE_SCHED_BALANCED, w, S) != TFHE_OK)
+            return -1.0;
+        double c = 0;
+        for (int l = 1; l <= S.depth; ++l) {
+            const long n = S.level_off[l] - S.level_off[l - 1];
+            c += (double)((n + w - 1) / w) * t;
+        }
+        return c;
+    };
+    const double c4 = cost(w4, t4), c5 = cost(w5, t5);
+    const long pick = (c4 >= 0 && c5 >= 0 && c5 < 0.99 * c4) ? w5 : w4;
+    C.wave_choice[sig] = pick;
+    return pick;
+}
+
 int run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, cudaStream_t st)
 {
     if (!ctx->keys_loaded)
@@ -1078,9 +1117,12 @@ int run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, cudaStream_t st)
     if (njobs == 0)
         return TFHE_OK;
     CircuitCache &C = cache_of(ctx);
-    const long target = C.level_width > 0 ? C.level_width : 4L * ctx->num_sms;
-    const std::string key = signature(jobs, njobs) + "|" + std::to_string(C.policy) + ":" +
-                            std::to_string(target);
+    const std::string sig = signature(jobs, njobs);
+    long target = C.level_width > 0 ? C.level_width : 4L * ctx->num_sms;
+    if (C.level_width == 0 && C.policy == TFHE_SCHED_BALANCED)
+        target = choose_wave(ctx, C, sig, jobs, njobs);
+    const int wide = target == 5L * ctx->num_sms && C.level_width == 0 ? kBrFive : 0;
+    const std::string key = sig + "|" + std::to_string(C.policy) + ":" + std::to_string(target);
     auto it = C.plans.find(key);
     if (it == C.plans.end()) {
         std::unique_ptr<Plan> P(new Plan());
@@ -1094,6 +1136,8 @@ int run_jobs(tfhe_ctx *ctx, const tfhe_job *jobs, size_t njobs, cudaStream_t st)
             C.plans.erase(C.order.front());
             C.order.erase(C.order.begin());
         }
+        P->wave = target;
+        P->wide_shape = wide;
         C.order.push_back(key);
         it = C.plans.emplace(key, std::move(P)).first;
     }
@@ -1262,8 +1306,8 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
     case TFHE_OPT_BR_GROUP:
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != kBrSplit &&
             value != kBrPair && value != kBrStaged && value != kBrStagedCtl &&
-            value != kBrSplitStaged)
-            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 8, 16, 32, 33 or 40");
+            value != kBrSplitStaged && value != kBrFive)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 5, 8, 16, 32, 33 or 40");
         ctx->keys.br_group = (int)value;
         invalidate_graphs(ctx);   // captured graphs hold the old launch shape
         return TFHE_OK;

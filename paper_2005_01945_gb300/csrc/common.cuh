@@ -83,6 +83,10 @@ constexpr int kBrStagedCtl = 33;
 // One bootstrap on 8 warps with the key staged (the latency shape, whose
 // single pointwise warp per sub-partition otherwise waits on L2 each step).
 constexpr int kBrSplitStaged = 40;
+// One bootstrap per 4-warp CTA compiled for five CTAs per SM (96 registers,
+// 20 warps): one wave is 5 bootstraps per SM, for schedules whose levels
+// fill such waves.
+constexpr int kBrFive = 5;
 // Key-switch launch code for the tiled kernel (shared-memory key stages);
 // the codes 1 .. 32 are j-chunks of the direct kernel.
 constexpr int kKsTiled = 64;
@@ -103,6 +107,9 @@ struct DevKeys {
     // covers widths up to kTuneEdge[b] (the last bucket is unbounded).
     int8_t tune_br[8];     // bootstraps per blind-rotation CTA
     int8_t tune_ks[8];     // key-switch kernel: kKsTiled, or j-chunks 1 .. 32
+    // Autotuned time (ms) of one full blind-rotation wave: [0] 4 bootstraps
+    // per SM (the tuned shape), [1] 5 per SM (kBrFive); 0 = not measured.
+    float wave_ms[2];
 };
 
 constexpr long kTuneEdge[8] = {152, 304, 608, 1216, 2432, 4864, 9728, 1L << 40};

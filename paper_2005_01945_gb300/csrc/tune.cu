@@ -53,14 +53,18 @@ static bool load_cache(const char *path, const std::string &key, DevKeys &k)
     while (std::fgets(line, sizeof(line), f)) {
         char kbuf[256];
         int br[8], ks[8];
-        if (std::sscanf(line, "%255s br %d %d %d %d %d %d %d %d ks %d %d %d %d %d %d %d %d", kbuf,
-                        &br[0], &br[1], &br[2], &br[3], &br[4], &br[5], &br[6], &br[7], &ks[0],
-                        &ks[1], &ks[2], &ks[3], &ks[4], &ks[5], &ks[6], &ks[7]) == 17 &&
-            key == kbuf) {
+        float wv[2] = {0.f, 0.f};
+        const int got = std::sscanf(
+            line, "%255s br %d %d %d %d %d %d %d %d ks %d %d %d %d %d %d %d %d waves %f %f", kbuf,
+            &br[0], &br[1], &br[2], &br[3], &br[4], &br[5], &br[6], &br[7], &ks[0], &ks[1],
+            &ks[2], &ks[3], &ks[4], &ks[5], &ks[6], &ks[7], &wv[0], &wv[1]);
+        if ((got == 17 || got == 19) && key == kbuf) {
             for (int b = 0; b < 8; ++b) {
                 k.tune_br[b] = (int8_t)br[b];
                 k.tune_ks[b] = (int8_t)ks[b];
             }
+            k.wave_ms[0] = got == 19 ? wv[0] : 0.f;
+            k.wave_ms[1] = got == 19 ? wv[1] : 0.f;
             found = true;
         }
     }
@@ -79,7 +83,7 @@ static void save_cache(const char *path, const std::string &key, const DevKeys &
     std::fprintf(f, " ks");
     for (int b = 0; b < 8; ++b)
         std::fprintf(f, " %d", k.tune_ks[b]);
-    std::fprintf(f, "\n");
+    std::fprintf(f, " waves %.4f %.4f\n", k.wave_ms[0], k.wave_ms[1]);
     std::fclose(f);
 }
 
@@ -180,6 +184,34 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
                 }
             }
         }
+        // one full wave at 4 bootstraps per SM (the tuned shape of that
+        // width) and at 5 per SM: the level schedules pick their wave size
+        // from these times
+        float wave[2] = {0.f, 0.f};
+        std::memcpy(K.tune_br, br, sizeof(br));
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            const long W = (v == 0 ? 4L : 5L) * ctx->num_sms;
+            if (W > maxw)
+                break;
+            K.br_group = v == 0 ? 0 : kBrFive;
+            float tot = 0;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    e = launch_blind_rotate(K, nullptr, cts, nullptr, W, nullptr, nullptr, 0, big,
+                                            W, kMu, ctx->status, ctx->br_grid, st);
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess)
+                    e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    tot += ms;
+            }
+            wave[v] = tot / 3.f;
+        }
+        K.wave_ms[0] = wave[0];
+        K.wave_ms[1] = wave[1];
         K.br_group = saved_group;
         keyswitch_force_chunks(0);
         cudaFree(cts);

@@ -163,6 +163,9 @@ def test_mixed_jobs_and_schedules_agree(small):
 @pytest.fixture(scope="module")
 def full(orc):
     e = Env(orc, 500, synth.MASTER_SEED)
+    # the launch configuration the benchmark times: tuned CTA shapes and
+    # key-switch kernels, and the wave size each schedule picks from them
+    e.ctx.autotune()
     yield e
     e.ctx.close()
 

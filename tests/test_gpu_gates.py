@@ -275,10 +275,11 @@ def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
     assert np.array_equal(got[sample, :p.n + 1], want)
 
 
-@pytest.mark.parametrize("group", [1, 2, 4, 8, 16, 32, 33, 40])
+@pytest.mark.parametrize("group", [1, 2, 4, 5, 8, 16, 32, 33, 40])
 def test_each_lockstep_group_bit_exact(gpu, orc, group):
     """Blind rotation with 1, 2 or 4 bootstraps per CTA (13 gates leave empty
-    slots in the last group, and skipped CMux steps in some slots), with one
+    slots in the last group, and skipped CMux steps in some slots), one per
+    4-warp CTA compiled for 5 CTAs per SM (shape 5), with one
     bootstrap spread over 8 warps (shape 8), with one bootstrap on a
     cluster of two CTAs exchanging residues (shape 16), and with two per
     CTA reading the key from bulk-copied shared-memory stages (shape 32) or,
