@@ -527,24 +527,32 @@ void input_groups(int kind, int w, int rows, int cols, long &rows0, long &rows1)
 // Compiled plans
 // ---------------------------------------------------------------------
 
-__global__ void k_gather_rows_impl(int32_t *dst, const int32_t *__restrict__ src,
-                              const int32_t *__restrict__ rows, long count)
+__global__ void k_gather_rows_impl(int32_t *dst, const int32_t *__restrict__ src, long src_rows,
+                                   const int32_t *__restrict__ rows, long count,
+                                   uint32_t *status)
 {
     const long r = blockIdx.x;
     if (r >= count)
         return;
-    const int4 *s = reinterpret_cast<const int4 *>(src + (long)rows[r] * kLweStride);
+    const long sr = rows[r];
+    if (sr < 0 || sr >= src_rows) {
+        if (threadIdx.x == 0)
+            atomicOr(status, kErrGather);
+        return;
+    }
+    const int4 *s = reinterpret_cast<const int4 *>(src + sr * kLweStride);
     int4 *d = reinterpret_cast<int4 *>(dst + r * kLweStride);
     for (int k = threadIdx.x; k < kLweStride / 4; k += blockDim.x)
         d[k] = s[k];
 }
 
-cudaError_t launch_gather_rows(int32_t *dst, const int32_t *src, const int32_t *rows, long count,
+cudaError_t launch_gather_rows(int32_t *dst, const int32_t *src, long src_rows,
+                               const int32_t *rows, long count, uint32_t *status,
                                cudaStream_t st)
 {
     if (count <= 0)
         return cudaSuccess;
-    k_gather_rows_impl<<<(unsigned)count, 128, 0, st>>>(dst, src, rows, count);
+    k_gather_rows_impl<<<(unsigned)count, 128, 0, st>>>(dst, src, src_rows, rows, count, status);
     return cudaGetLastError();
 }
 
@@ -1070,7 +1078,8 @@ static int run_plan(tfhe_ctx *ctx, Plan &P, const tfhe_job *jobs, cudaStream_t s
         const long cnt = L.n_out * L.batch;
         if (cnt == 0)
             continue;
-        e = launch_gather_rows(jobs[j].out, P.pool, P.d_out_rows + L.out_off, cnt, st);
+        e = launch_gather_rows(jobs[j].out, P.pool, P.pool_rows, P.d_out_rows + L.out_off, cnt,
+                               ctx->status, st);
         ctx->launches += 1;
     }
     if (e != cudaSuccess)

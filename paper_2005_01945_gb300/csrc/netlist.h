@@ -60,7 +60,10 @@ std::shared_ptr<const Netlist> get_netlist(int kind, int w, int rows, int cols);
 void input_groups(int kind, int w, int rows, int cols, long &rows0, long &rows1);
 
 // Copies count ciphertext rows src[rows[i]] -> dst[i].
-cudaError_t launch_gather_rows(int32_t *dst, const int32_t *src, const int32_t *rows, long count,
+// dst row r = src row rows[r]; an index outside [0, src_rows) sets
+// kErrGather in *status and leaves dst row r unwritten.
+cudaError_t launch_gather_rows(int32_t *dst, const int32_t *src, long src_rows,
+                               const int32_t *rows, long count, uint32_t *status,
                                cudaStream_t st);
 
 }  // namespace tgb

@@ -559,7 +559,8 @@ static void srv_loop(Server *Sp)
         for (SrvReq *r : finishing) {
             const long no = (long)r->nl->out.size();
             if (e == cudaSuccess)
-                e = launch_gather_rows(r->r.out, S.pool, I.d_out + o, no, S.st);
+                e = launch_gather_rows(r->r.out, S.pool, S.pool_rows, I.d_out + o, no,
+                                       ctx->status, S.st);
             o += no;
         }
         if (e == cudaSuccess)
