@@ -81,6 +81,9 @@ def parse():
                     help="one-launch-pair-per-gate runs of the sequential multiplier")
     ap.add_argument("--per-gate-samples-shallow", type=int, default=10,
                     help="one-launch-pair-per-gate runs of the Dadda multiplier")
+    ap.add_argument("--product-choice", type=int, default=2432,
+                    help="bootstraps of the tensor-pipe vs NTT CMux comparison in the bench line "
+                         "(a multiple of 128; 0: skip)")
     ap.add_argument("--config-steps", type=int, default=3,
                     help="timed steps of configs 2 and 3 (after one warm-up step)")
     ap.add_argument("--cpu-gates-single", type=int, default=8,
@@ -299,28 +302,21 @@ def run_br_only(count, group=0):
     ctx.close()
 
 
-def run_tc_products(count, reps=5):
+def tc_vs_ntt(ctx, p, kd, count, reps=5, device="cuda"):
     """The exact-product choice, measured: one CMux step's 8 negacyclic
     products on the tensor pipe (tcgen05, limb-split bf16, exact fp32 sums)
     for `count` bootstraps, against the NTT blind rotation of the same count
     (n = 500 CMux steps, each with decomposition, 12 transforms, pointwise
     products, CRT and accumulation), per CMux step and bootstrap."""
     import torch
-    from paper_2005_01945_gb300 import api, build, synth
-    build.build()
-    p = synth.TFHEParams()
+    from paper_2005_01945_gb300 import api, synth
     g = synth._gen(9, "tc_bench")
-    d = api.to_device
-    kd = synth.key_draws(p, synth.MASTER_SEED)
-    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
-                         d(kd.ksk_noise))
-    ctx = api.Context(p)
-    ctx.set_keys(bk, ksk)
+    d = lambda a: api.to_device(a, device)  # noqa: E731
     rows = d(g.integers(0, 1 << 32, size=(4, 2, 1024), dtype=np.uint64).astype(np.uint32))
     dig = d(g.integers(-512, 512, size=(count, 4, 1024), dtype=np.int64).astype(np.int32))
-    key_ops = torch.empty(api.tc_key_bytes(), dtype=torch.uint8, device="cuda")
-    digit_ops = torch.empty(api.tc_digit_bytes(count), dtype=torch.uint8, device="cuda")
-    out = torch.empty((count, 2, 1024), dtype=torch.int32, device="cuda")
+    key_ops = torch.empty(api.tc_key_bytes(), dtype=torch.uint8, device=device)
+    digit_ops = torch.empty(api.tc_digit_bytes(count), dtype=torch.uint8, device=device)
+    out = torch.empty((count, 2, 1024), dtype=torch.int32, device=device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
@@ -337,29 +333,43 @@ def run_tc_products(count, reps=5):
 
     prep_ms = timed(lambda: ctx.tc_prepare_key(rows, key_ops))
     tc_ms = timed(lambda: ctx.cmux_products_tc(dig, key_ops, digit_ops, out))
-    # the NTT path: blind rotation + extraction of `count` gates (500 CMux)
     bits = synth.random_bits((2, count), 7, "tcntt")
     cd = synth.ct_draws(p, (2, count), 7, "tcntt")
     s_dev = d(kd.s)
     ca = api.encrypt_bits(p, s_dev, d(cd.mask[0]), d(cd.noise[0]), d(bits[0]))
     cb = api.encrypt_bits(p, s_dev, d(cd.mask[1]), d(cd.noise[1]), d(bits[1]))
     ops = d(np.full(count, 3, np.uint8))
-    big = torch.empty((count, api.BIG_STRIDE), dtype=torch.int32, device="cuda")
+    big = torch.empty((count, api.BIG_STRIDE), dtype=torch.int32, device=device)
     br_ms = timed(lambda: ctx.blind_rotate_extract(ops, ca, cb, big))
-    peaks = measured_peaks()
-    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    bf16 = float(measured_peaks().get("bf16_tflops", 1900.0))
     flops = 2.0 * 8 * 4096 * 2048 * count          # 8 limb pairs x (M x 4N x 2N)
     tc_best = min(tc_ms)
     ntt_cmux_ns = min(br_ms) * 1e6 / (p.n * count)
-    print(json.dumps({
-        "tc_products": count, "status": ctx.status(),
-        "tc_prepare_key_ms": prep_ms, "tc_products_ms": tc_ms,
-        "tc_ns_per_cmux_bootstrap": tc_best * 1e6 / count,
-        "tc_tflops": flops / (tc_best / 1e3) / 1e12,
-        "tc_frac_of_bf16_peak": flops / (tc_best / 1e3) / 1e12 / bf16,
-        "tc_ns_per_cmux_bootstrap_at_peak": flops / (bf16 * 1e12) * 1e9 / count,
-        "ntt_blind_rotation_ms": br_ms, "ntt_ns_per_cmux_bootstrap": ntt_cmux_ns,
-        "tc_over_ntt": (tc_best * 1e6 / count) / ntt_cmux_ns}), flush=True)
+    return {"bootstraps": count, "status": ctx.status(),
+            "tc_prepare_key_ms": prep_ms, "tc_products_ms": tc_ms,
+            "tc_ns_per_cmux_bootstrap": tc_best * 1e6 / count,
+            "tc_tflops": flops / (tc_best / 1e3) / 1e12,
+            "tc_frac_of_bf16_peak": flops / (tc_best / 1e3) / 1e12 / bf16,
+            "tc_ns_per_cmux_bootstrap_at_peak": flops / (bf16 * 1e12) * 1e9 / count,
+            "ntt_blind_rotation_ms": br_ms, "ntt_ns_per_cmux_bootstrap": ntt_cmux_ns,
+            "tc_over_ntt": (tc_best * 1e6 / count) / ntt_cmux_ns,
+            "chosen": "ntt" if tc_best * 1e6 / count > ntt_cmux_ns else "tensor"}
+
+
+def run_tc_products(count, reps=5):
+    """CLI mode of tc_vs_ntt with its own context and keys."""
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    p = synth.TFHEParams()
+    d = api.to_device
+    kd = synth.key_draws(p, synth.MASTER_SEED)
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    res = tc_vs_ntt(ctx, p, kd, count, reps)
+    res["tc_products"] = res.pop("bootstraps")
+    print(json.dumps(res), flush=True)
     ctx.close()
 
 
@@ -1004,6 +1014,13 @@ def main():
                                    f"parallel-prefix adder ({latency_tree['gates']:,} gates, "
                                    f"{latency_tree['levels']} levels) alone")
 
+    # ---- the exact-product choice: tensor-pipe CMux products vs the NTT CMux
+    product_choice = None
+    if rank == 0 and args.product_choice > 0:
+        product_choice = tc_vs_ntt(ctx, p, kd, args.product_choice, device=dev)
+        product_choice = {k: v for k, v in product_choice.items()
+                          if k not in ("tc_prepare_key_ms", "tc_products_ms", "ntt_blind_rotation_ms")}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
         sample = OracleSample(args.cpu_gates, seed)
@@ -1038,7 +1055,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "keyswitch": keyswitch,
-                "cpu_baseline": cpu, "configs": configs, "mul32_latency": latency,
+                "cpu_baseline": cpu, "configs": configs, "product_choice": product_choice,
+                "mul32_latency": latency,
                 "mul32_shallow_latency": latency_tree, "verified": verified}
         print(json.dumps(line), flush=True)
     ctx.close()
