@@ -1087,34 +1087,60 @@ static int run_plan(tfhe_ctx *ctx, Plan &P, const tfhe_job *jobs, cudaStream_t s
     return TFHE_OK;
 }
 
-// Wave size of a job mix's level schedule: 4 bootstraps per SM (the tuned
-// shapes) or 5 (kBrFive, 20 warps per SM).  Each level of a schedule built
-// for wave W costs about ceil(width / W) full waves; with the autotuner's
-// time of one full wave of each kind, the schedule with the lower total is
-// used, once it is at least 1 % cheaper.  Decided once per job mix.
+// Level unit of a job mix's schedule (the width the deadline scheduler
+// rounds levels up to): one bootstrap per SM (levels run at the tuned
+// narrow shape: lowest latency for a lone request), one wave of 4 per SM
+// (the tuned shapes), or one wave of 5 per SM (levels of a wave or more at
+// kBrFive).  Each candidate's schedule is costed with the autotuner's
+// measurements: a level of w gates costs the measured time of its width
+// bucket while w fits one 4-per-SM wave, ceil(w / wave) wave times above
+// (at 5 per SM for the 5-per-SM candidate), and the cheapest schedule is
+// used once it is at least 1 % cheaper than the 4-per-SM one.  Decided
+// once per job mix; without autotuner measurements the unit is one wave of
+// 4 per SM.
 static long choose_wave(tfhe_ctx *ctx, CircuitCache &C, const std::string &sig,
                         const tfhe_job *jobs, size_t njobs)
 {
-    const long w4 = 4L * ctx->num_sms, w5 = 5L * ctx->num_sms;
-    const float t4 = ctx->keys.wave_ms[0], t5 = ctx->keys.wave_ms[1];
-    if (!(t4 > 0.f && t5 > 0.f) || t5 / w5 >= 0.99f * t4 / w4)
+    const long w1 = ctx->num_sms, w4 = 4L * ctx->num_sms, w5 = 5L * ctx->num_sms;
+    const DevKeys &K = ctx->keys;
+    const float t4 = K.wave_ms[0], t5 = K.wave_ms[1];
+    if (!(t4 > 0.f))
         return w4;
     auto it = C.wave_choice.find(sig);
     if (it != C.wave_choice.end())
         return it->second;
-    auto cost = [&](long w, float t) -> double {
+    auto level_cost = [&](long n, long unit) -> double {
+        if (unit == w5 && n >= w5)
+            return (double)((n + w5 - 1) / w5) * t5;
+        if (n > w4)
+            return (double)((n + w4 - 1) / w4) * t4;
+        const int b = tune_bucket(n);
+        return K.tune_ms[b] > 0.f ? K.tune_ms[b] : t4;
+    };
+    auto cost = [&](long unit) -> double {
         Schedule S;
-        if (build_schedule(nullptr, jobs, njobs, TFHE_SCHED_BALANCED, w, S) != TFHE_OK)
+        if (build_schedule(nullptr, jobs, njobs, TFHE_SCHED_BALANCED, unit, S) != TFHE_OK)
             return -1.0;
         double c = 0;
-        for (int l = 1; l <= S.depth; ++l) {
-            const long n = S.level_off[l] - S.level_off[l - 1];
-            c += (double)((n + w - 1) / w) * t;
-        }
+        for (int l = 1; l <= S.depth; ++l)
+            c += level_cost(S.level_off[l] - S.level_off[l - 1], unit);
         return c;
     };
-    const double c4 = cost(w4, t4), c5 = cost(w5, t5);
-    const long pick = (c4 >= 0 && c5 >= 0 && c5 < 0.99 * c4) ? w5 : w4;
+    const double c4 = cost(w4);
+    long pick = w4;
+    double best = c4;
+    if (c4 >= 0) {
+        if (K.tune_ms[0] > 0.f && w1 <= kTuneEdge[0]) {
+            const double c1 = cost(w1);
+            if (c1 >= 0 && c1 < 0.99 * best)
+                pick = w1, best = c1;
+        }
+        if (t5 > 0.f && t5 / w5 < 0.99f * t4 / w4) {
+            const double c5 = cost(w5);
+            if (c5 >= 0 && c5 < 0.99 * best)
+                pick = w5, best = c5;
+        }
+    }
     C.wave_choice[sig] = pick;
     return pick;
 }

@@ -110,6 +110,9 @@ struct DevKeys {
     // Autotuned time (ms) of one full blind-rotation wave: [0] 4 bootstraps
     // per SM (the tuned shape), [1] 5 per SM (kBrFive); 0 = not measured.
     float wave_ms[2];
+    // Autotuned time (ms) of a level at each bucket's widest width with the
+    // bucket's chosen shape; 0 = not measured.
+    float tune_ms[8];
 };
 
 constexpr long kTuneEdge[8] = {152, 304, 608, 1216, 2432, 4864, 9728, 1L << 40};

@@ -267,10 +267,13 @@ struct GrowPool {
     void release()
     {
         if (api) {
-            if (mapped)
-                api->unmap(base, mapped);
-            for (auto &c : chunks)
+            // each mapping is undone as it was made, chunk by chunk
+            size_t off = 0;
+            for (auto &c : chunks) {
+                api->unmap(base + off, c.second);
                 api->release(c.first);
+                off += c.second;
+            }
             if (base)
                 api->addr_free(base, reserved);
         } else if (base) {

@@ -53,18 +53,22 @@ static bool load_cache(const char *path, const std::string &key, DevKeys &k)
     while (std::fgets(line, sizeof(line), f)) {
         char kbuf[256];
         int br[8], ks[8];
-        float wv[2] = {0.f, 0.f};
+        float wv[2] = {0.f, 0.f}, tm[8] = {0.f};
         const int got = std::sscanf(
-            line, "%255s br %d %d %d %d %d %d %d %d ks %d %d %d %d %d %d %d %d waves %f %f", kbuf,
-            &br[0], &br[1], &br[2], &br[3], &br[4], &br[5], &br[6], &br[7], &ks[0], &ks[1],
-            &ks[2], &ks[3], &ks[4], &ks[5], &ks[6], &ks[7], &wv[0], &wv[1]);
-        if ((got == 17 || got == 19) && key == kbuf) {
+            line,
+            "%255s br %d %d %d %d %d %d %d %d ks %d %d %d %d %d %d %d %d waves %f %f "
+            "levels %f %f %f %f %f %f %f %f",
+            kbuf, &br[0], &br[1], &br[2], &br[3], &br[4], &br[5], &br[6], &br[7], &ks[0], &ks[1],
+            &ks[2], &ks[3], &ks[4], &ks[5], &ks[6], &ks[7], &wv[0], &wv[1], &tm[0], &tm[1],
+            &tm[2], &tm[3], &tm[4], &tm[5], &tm[6], &tm[7]);
+        if ((got == 17 || got == 19 || got == 27) && key == kbuf) {
             for (int b = 0; b < 8; ++b) {
                 k.tune_br[b] = (int8_t)br[b];
                 k.tune_ks[b] = (int8_t)ks[b];
+                k.tune_ms[b] = got == 27 ? tm[b] : 0.f;
             }
-            k.wave_ms[0] = got == 19 ? wv[0] : 0.f;
-            k.wave_ms[1] = got == 19 ? wv[1] : 0.f;
+            k.wave_ms[0] = got >= 19 ? wv[0] : 0.f;
+            k.wave_ms[1] = got >= 19 ? wv[1] : 0.f;
             found = true;
         }
     }
@@ -83,7 +87,10 @@ static void save_cache(const char *path, const std::string &key, const DevKeys &
     std::fprintf(f, " ks");
     for (int b = 0; b < 8; ++b)
         std::fprintf(f, " %d", k.tune_ks[b]);
-    std::fprintf(f, " waves %.4f %.4f\n", k.wave_ms[0], k.wave_ms[1]);
+    std::fprintf(f, " waves %.4f %.4f levels", k.wave_ms[0], k.wave_ms[1]);
+    for (int b = 0; b < 8; ++b)
+        std::fprintf(f, " %.4f", k.tune_ms[b]);
+    std::fprintf(f, "\n");
     std::fclose(f);
 }
 
@@ -123,6 +130,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
         }
         const int saved_group = K.br_group;
         int8_t br[8] = {0}, ks[8] = {0};
+        float level_ms[8] = {0.f};
         for (int b = 0; b < 8 && e == cudaSuccess; ++b) {
             const long W = widths[b];
             // candidates from the finest launch granularity up: a later one
@@ -156,6 +164,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
                 if (e == cudaSuccess && (br[b] == 0 || tot < 0.98f * best)) {
                     best = tot;
                     br[b] = (int8_t)B;
+                    level_ms[b] = tot / 2.f;   // two timed runs
                 }
             }
             best = 1e30f;
@@ -212,6 +221,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
         }
         K.wave_ms[0] = wave[0];
         K.wave_ms[1] = wave[1];
+        std::memcpy(K.tune_ms, level_ms, sizeof(level_ms));
         K.br_group = saved_group;
         keyswitch_force_chunks(0);
         cudaFree(cts);

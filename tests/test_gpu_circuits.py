@@ -230,6 +230,31 @@ def test_shallow_circuits_full_parameters_decrypt(full):
     assert E.ctx.status() == 0
 
 
+def test_lone_request_schedules_agree(full):
+    """One 32-bit multiplication alone (sequential and Dadda) at n = 500 in
+    the tuned configuration, where the schedule may round levels to one
+    bootstrap per SM for latency, and again with levels forced to waves of
+    608 gates: the ciphertexts are identical word for word and decrypt to
+    the product."""
+    E = full
+    api = E.api
+    a, b = synth.int_pairs(1, 32, 91, "lone")
+    da, _ = E.enc_ints(a, 32, 91, "lonea")
+    db, _ = E.enc_ints(b, 32, 91, "loneb")
+    for kind in (api.MUL_DADDA, api.MUL):
+        R1, R2 = E.out((1, 32)), E.out((1, 32))
+        E.ctx.run_jobs([dict(kind=kind, width=32, batch=1, in0=da, in1=db, out=R1)])
+        E.ctx.set_option(api.OPT_LEVEL_WIDTH, 608)
+        try:
+            E.ctx.run_jobs([dict(kind=kind, width=32, batch=1, in0=da, in1=db, out=R2)])
+        finally:
+            E.ctx.set_option(api.OPT_LEVEL_WIDTH, 0)
+        g1, g2 = E.host(R1), E.host(R2)
+        assert np.array_equal(g1, g2)
+        assert np.array_equal(E.dec_ints(g1), (a * b) % (1 << 32))
+    assert E.ctx.status() == 0
+
+
 def test_config2_mul16_mul32_mixed(full):
     """64 16-bit and 64 32-bit multiplications in one schedule (222,208
     bootstraps, uneven depths 56 and 120), n = 500: every product decrypts
