@@ -157,8 +157,10 @@ int tfhe_keyswitch(tfhe_ctx *ctx, const int32_t *big, int32_t *out, size_t count
  * Z[X]/(X^1024 + 1) mod 2^32, r < 4, p < 2 -- the 8 products the NTT path
  * computes per CMux -- as tcgen05 matrix products of limb-split bf16
  * operands with exact fp32 sums (digits split in 2 limbs, key words in 4
- * balanced bytes).  The blind-rotation kernels do not use it: on GB300 it
- * is slower than the NTT (measurements in the design notes).
+ * balanced bytes).  The blind-rotation kernels do not use it: on GB300 the
+ * 8 products take about 6 times as long as a whole NTT CMux step (160 ns
+ * against 26 ns per bootstrap), and would still take 2.6 times as long at
+ * the full bf16 tensor rate.
  *   tfhe_tc_prepare_key: bk_rows = device uint32 [4 rows][2 polys][1024]
  *     (one TGSW key sample in coefficient form, row r = c l + j) ->
  *     key_ops, a caller-owned device buffer of tfhe_tc_key_bytes() bytes
