@@ -316,8 +316,9 @@ typedef enum {
                              /*    per SM), 33 = the same shape and occupancy with  */
                              /*    the key read through L1 (the staging's control), */
                              /*    40 = one bootstrap on 8 warps with the key       */
-                             /*    staged, or 0 (default): autotuned, else by       */
-                             /*    batch size                                       */
+                             /*    staged, 48 = the two-CTA cluster with each CTA's */
+                             /*    half of the key staged, or 0 (default):          */
+                             /*    autotuned, else by batch size                    */
     TFHE_OPT_SCHEDULE = 4,   /* tfhe_schedule policy of circuit schedules           */
     TFHE_OPT_LEVEL_WIDTH = 5,/* target gates per level for BALANCED (0: one wave    */
                              /*    of 4 bootstraps per SM, or of 5 per SM (shape 5) */

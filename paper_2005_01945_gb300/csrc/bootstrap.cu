@@ -847,7 +847,38 @@ struct PairSmem {
     uint16_t abar[kLweStride];
 };
 
+// Key stage of the cluster shape (kBrPairStaged): this CTA's prime half of
+// the next CMux step's key, 2 polynomials x 16 KB, bulk-copied while the
+// current step runs (double buffer).
+struct PairStage {
+    uint4 bk[2][2][kN];         // [buffer][poly p][reg*32+lane]
+    unsigned long long full[2];
+    uint32_t issued[2];
+    volatile int abort;         // a wait ran out: read the key from global memory
+};
+
+__device__ __forceinline__ void pair_issue(PairStage &G, const uint4 *bk_ntt, int i, int rank,
+                                           int buf)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     br_saddr(&G.full[buf])),
+                 "r"((uint32_t)(2 * kN * sizeof(uint4)))
+                 : "memory");
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                     "[%0], [%1], %2, [%3];" ::"r"(br_saddr(&G.bk[buf][p][0])),
+                     "l"(bk_ntt + (((long)i * 2 + p) * 2 + rank) * kN),
+                     "r"((uint32_t)(kN * sizeof(uint4))), "r"(br_saddr(&G.full[buf]))
+                     : "memory");
+    G.issued[buf]++;
+}
+
 // Pointwise products of rows r0 .. r0 + 15 of output polynomial p.
+// SH: bkp points into the shared-memory key stage (ld.shared), else to the
+// key in global memory (through L1).
+template <bool SH>
 __device__ __forceinline__ void pair_pointwise(PairSmem &S, const uint4 *__restrict__ bkp, int p,
                                                int r0, int lane, const Prime &pr)
 {
@@ -855,7 +886,13 @@ __device__ __forceinline__ void pair_pointwise(PairSmem &S, const uint4 *__restr
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
         const int e = (r0 + rr) * 32 + lane;
-        const uint4 b = __ldg(bkp + e);
+        uint4 b;
+        if (SH)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                         : "r"(br_saddr(bkp) + (uint32_t)e * 16u));
+        else
+            b = __ldg(bkp + e);
         uint64_t s = (uint64_t)S.fwd[0][e] * b.x;
         s += (uint64_t)S.fwd[1][e] * b.y;
         s += (uint64_t)S.fwd[2][e] * b.z;
@@ -875,10 +912,12 @@ __device__ __forceinline__ void pair_pointwise(PairSmem &S, const uint4 *__restr
 // barrier arrival of the step between in between.  Control flow is the
 // same in both CTAs of a cluster (same gate, same abar), so every cluster
 // barrier is reached by both.
+template <int STAGE>
 __global__ void __launch_bounds__(256, 1) k_blind_rotate_pair(const BrArgs A)
 {
     extern __shared__ uint4 smem_raw[];
     PairSmem &S = *reinterpret_cast<PairSmem *>(smem_raw);
+    PairStage &G = *reinterpret_cast<PairStage *>(reinterpret_cast<PairSmem *>(smem_raw) + 1);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -887,23 +926,64 @@ __global__ void __launch_bounds__(256, 1) k_blind_rotate_pair(const BrArgs A)
     const Prime pr((uint32_t)rank);
     const long nclusters = gridDim.x / 2, cid = blockIdx.x / 2;
     int par = 0;
+    uint32_t uses = 0;   // staged steps so far (the same in every thread)
+    if (STAGE) {
+        if (tid == 0) {
+            for (int b = 0; b < 2; ++b) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(br_saddr(&G.full[b]))
+                             : "memory");
+                G.issued[b] = 0;
+            }
+            G.abort = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     for (long g = cid; g < A.count; g += nclusters) {
         const bool active = br_prologue<256>(A, g, tid, S.abar, rank == 0);
+        if (STAGE && tid == 0 && n > 0 && !G.abort)
+            pair_issue(G, A.keys.bk_ntt, 0, rank, uses & 1);
         __syncthreads();
         br_acc_init<256>(A, S.acc, S.abar[n], tid);
         __syncthreads();
         for (int i = 0; i < n; ++i) {
+            const uint32_t u = uses;   // this step's use of buffer u & 1
+            if (STAGE) {
+                ++uses;
+                // the other buffer was last read in step i - 1, before the
+                // barrier that ended that step's pointwise phase
+                if (tid == 0 && i + 1 < n && !G.abort)
+                    pair_issue(G, A.keys.bk_ntt, i + 1, rank, (u + 1) & 1);
+            }
             const int a = S.abar[i];
-            if (a == 0)
-                continue;   // X^0 acc - acc = 0: nothing changes (in both CTAs)
+            if (a == 0) {
+                // X^0 acc - acc = 0: nothing changes (in both CTAs); the
+                // step's copy still has to land before its buffer is reused
+                if (STAGE && tid == 0 && !G.abort && !bk_wait(&G.full[u & 1], (u >> 1) & 1)) {
+                    G.abort = 1;
+                    atomicOr(A.status, kErrTimeout);
+                }
+                continue;
+            }
             uint32_t x[32];
             if (warp < 4)
                 digit_fwd(x, S.acc[warp >> 1], S.fwd[warp], warp & 1, a, lane, A.keys.twb, pr);
             __syncthreads();
             if (warp < 4) {
                 const int p = warp >> 1;
-                pair_pointwise(S, A.keys.bk_ntt + (((long)i * 2 + p) * 2 + rank) * 1024, p,
-                               16 * (warp & 1), lane, pr);
+                bool staged = false;
+                if (STAGE) {
+                    staged = !G.abort && bk_wait(&G.full[u & 1], (u >> 1) & 1);
+                    if (!staged && !G.abort) {
+                        G.abort = 1;   // read this and later steps from global memory
+                        atomicOr(A.status, kErrTimeout);
+                    }
+                }
+                if (staged)
+                    pair_pointwise<true>(S, &G.bk[u & 1][p][0], p, 16 * (warp & 1), lane, pr);
+                else
+                    pair_pointwise<false>(S, A.keys.bk_ntt + (((long)i * 2 + p) * 2 + rank) * 1024,
+                                          p, 16 * (warp & 1), lane, pr);
             }
             __syncthreads();
             if (warp < 2) {
@@ -932,6 +1012,12 @@ __global__ void __launch_bounds__(256, 1) k_blind_rotate_pair(const BrArgs A)
         __syncthreads();
     }
     cl.sync();   // the partner may still read this CTA's residues
+    // after a wait that ran out: copies still in flight land before the
+    // CTA's shared memory is released (the last use of each buffer)
+    if (STAGE && tid == 0 && G.abort)
+        for (int b = 0; b < 2; ++b)
+            if (G.issued[b])
+                (void)bk_wait(&G.full[b], (G.issued[b] - 1) & 1);
 }
 
 // ---------------------------------------------------------------------
@@ -1109,7 +1195,7 @@ int br_blocks_per_sm()
 static bool br_shape_ok(int v)
 {
     return v == 1 || v == 2 || v == 4 || v == kBrSplit || v == kBrPair || v == kBrStaged ||
-           v == kBrStagedCtl || v == kBrSplitStaged || v == kBrFive;
+           v == kBrStagedCtl || v == kBrSplitStaged || v == kBrFive || v == kBrPairStaged;
 }
 
 static int br_group(long count, int num_sms, int forced, const int8_t *tuned)
@@ -1152,20 +1238,22 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int shape = br_group(count, sms > 0 ? sms : 1, keys.br_group, keys.tune_br);
-    if (shape == kBrPair) {
-        static int prepared[64] = {0};
-        if (dev >= 0 && dev < 64 && !prepared[dev]) {
-            cudaFuncSetAttribute(k_blind_rotate_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(PairSmem));
+    if (shape == kBrPair || shape == kBrPairStaged) {
+        const bool staged = shape == kBrPairStaged;
+        const size_t smem = sizeof(PairSmem) + (staged ? sizeof(PairStage) : 0);
+        static int prepared[2][64] = {{0}};
+        if (dev >= 0 && dev < 64 && !prepared[staged][dev]) {
+            cudaFuncSetAttribute(staged ? k_blind_rotate_pair<1> : k_blind_rotate_pair<0>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             (void)cudaGetLastError();
-            prepared[dev] = 1;
+            prepared[staged][dev] = 1;
         }
         const long pairs = sms >= 2 ? sms / 2 : 1;   // one CTA per SM
         const long clusters = count < pairs ? count : pairs;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * clusters));
         cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = sizeof(PairSmem);
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1174,7 +1262,8 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_blind_rotate_pair, A);
+        return staged ? cudaLaunchKernelEx(&cfg, k_blind_rotate_pair<1>, A)
+                      : cudaLaunchKernelEx(&cfg, k_blind_rotate_pair<0>, A);
     }
     const int B = (shape == kBrSplit || shape == kBrSplitStaged || shape == kBrFive) ? 1
                 : (shape == kBrStaged || shape == kBrStagedCtl) ? 2 : shape;

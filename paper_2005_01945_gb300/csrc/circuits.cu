@@ -1341,8 +1341,8 @@ int tfhe_ctx_set_option(tfhe_ctx *ctx, int option, int64_t value)
     case TFHE_OPT_BR_GROUP:
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != kBrSplit &&
             value != kBrPair && value != kBrStaged && value != kBrStagedCtl &&
-            value != kBrSplitStaged && value != kBrFive)
-            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 5, 8, 16, 32, 33 or 40");
+            value != kBrSplitStaged && value != kBrFive && value != kBrPairStaged)
+            return fail(ctx, TFHE_EINVAL, "TFHE_OPT_BR_GROUP must be 0, 1, 2, 4, 5, 8, 16, 32, 33, 40 or 48");
         ctx->keys.br_group = (int)value;
         invalidate_graphs(ctx);   // captured graphs hold the old launch shape
         return TFHE_OK;

@@ -83,6 +83,8 @@ constexpr int kBrStagedCtl = 33;
 // One bootstrap on 8 warps with the key staged (the latency shape, whose
 // single pointwise warp per sub-partition otherwise waits on L2 each step).
 constexpr int kBrSplitStaged = 40;
+// One bootstrap on a two-CTA cluster with each CTA's half of the key staged.
+constexpr int kBrPairStaged = 48;
 // One bootstrap per 4-warp CTA compiled for five CTAs per SM (96 registers,
 // 20 warps): one wave is 5 bootstraps per SM, for schedules whose levels
 // fill such waves.

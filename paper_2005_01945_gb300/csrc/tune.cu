@@ -140,10 +140,11 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, const char *cache_path, int32_t 
             // levels end in part-filled waves that the finer shapes spread
             // over more SMs
             float best = 1e30f;
-            for (int B : {kBrSplit, kBrSplitStaged, kBrPair, 1, 2, 4, kBrStaged}) {
+            for (int B : {kBrSplit, kBrSplitStaged, kBrPair, kBrPairStaged, 1, 2, 4, kBrStaged}) {
                 // the latency shapes hold one bootstrap per SM (or SM pair):
                 // only candidates while a level fits in about one wave of them
-                if ((B == kBrSplit || B == kBrSplitStaged || B == kBrPair) &&
+                if ((B == kBrSplit || B == kBrSplitStaged || B == kBrPair ||
+                     B == kBrPairStaged) &&
                     W > 2L * ctx->num_sms)
                     continue;
                 K.br_group = B;

@@ -275,7 +275,7 @@ def test_many_gates_decrypt_and_sampled_parity(gpu, orc):
     assert np.array_equal(got[sample, :p.n + 1], want)
 
 
-@pytest.mark.parametrize("group", [1, 2, 4, 5, 8, 16, 32, 33, 40])
+@pytest.mark.parametrize("group", [1, 2, 4, 5, 8, 16, 32, 33, 40, 48])
 def test_each_lockstep_group_bit_exact(gpu, orc, group):
     """Blind rotation with 1, 2 or 4 bootstraps per CTA (13 gates leave empty
     slots in the last group, and skipped CMux steps in some slots), one per
@@ -283,8 +283,9 @@ def test_each_lockstep_group_bit_exact(gpu, orc, group):
     bootstrap spread over 8 warps (shape 8), with one bootstrap on a
     cluster of two CTAs exchanging residues (shape 16), and with two per
     CTA reading the key from bulk-copied shared-memory stages (shape 32) or,
-    at the same occupancy, through L1 (shape 33), and one bootstrap on 8
-    warps with the key staged (shape 40)."""
+    at the same occupancy, through L1 (shape 33), one bootstrap on 8 warps
+    with the key staged (shape 40), and the two-CTA cluster with each
+    CTA's half of the key staged (shape 48)."""
     torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
     count = 13
     bits, cts, dev = _fresh(gpu, orc, count, 40 + group, f"grp{group}", zero_some=True)
@@ -335,7 +336,7 @@ def test_autotune_keeps_results(gpu, orc):
     after = torch.zeros_like(before)
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], before)
     choices = gpu["ctx"].autotune()
-    assert set(choices["br_group"].values()) <= {1, 2, 4, 8, 16, 32, 40}
+    assert set(choices["br_group"].values()) <= {1, 2, 4, 8, 16, 32, 40, 48}
     assert set(choices["ks_chunks"].values()) <= {1, 2, 4, 8, 16, 32, api.KS_TILED}
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], after)
     assert torch.equal(before, after)
