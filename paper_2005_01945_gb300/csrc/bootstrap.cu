@@ -394,6 +394,16 @@ struct BkStage {
     volatile int abort;         // a wait ran out: read the key from global memory
 };
 constexpr uint32_t kBkStepBytes = 4 * kN * sizeof(uint4);   // 64 KB
+
+// The 8-warp shape's own transpose scratch and residue rows for its
+// inverse transforms (one bootstrap per CTA leaves the room), so that the
+// four warps go from their pointwise products straight into their inverse
+// transform without waiting for the others to finish reading the digit
+// transforms.
+struct SplitExtra {
+    uint32_t scratch[4][kSlot];  // transpose scratch of warp (p, h)
+    uint32_t xch[4][kN];         // residues [p * 2 + h][reg*32+lane], [0, q)
+};
 constexpr long kBkSpin = 1L << 20;                           // x ~1 us per try
 
 __device__ __forceinline__ uint32_t br_saddr(const void *p)
@@ -719,6 +729,9 @@ __global__ void __launch_bounds__(32 * W * B,
     const int bi = warp / W, wr = warp % W, tb = tid % T;   // bootstrap slot, role
     BrSmem &S = reinterpret_cast<BrSmem *>(smem_raw)[bi];
     BkStage &G = *reinterpret_cast<BkStage *>(reinterpret_cast<BrSmem *>(smem_raw) + B);
+    SplitExtra &X = *reinterpret_cast<SplitExtra *>(
+        reinterpret_cast<uint8_t *>(reinterpret_cast<BrSmem *>(smem_raw) + B) +
+        (STAGE ? sizeof(BkStage) : 0));
     const int lane_brv = brv5(lane);
     const int n = A.keys.n;
     const int w4 = wr & 3, p = w4 >> 1, h = wr & 1;
@@ -810,12 +823,16 @@ __global__ void __launch_bounds__(32 * W * B,
                         br_pointwise_staged(x, S, &G.bk[u & 1][p * 2 + h][0], lane, pr);
                     else
                         br_pointwise(x, S, bki, lane, pr);
+                    // straight on: the inverse writes only this warp's own
+                    // scratch and residue row
+                    inv_ntt(x, X.scratch[w4], lane, lane_brv, A.keys.twb, pr);
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        X.xch[w4][r * 32 + lane] = csub(x[r], pr.q);
                 }
                 __syncthreads();
-                if (wr < 4)
-                    br_inverse(x, S, w4, lane, lane_brv, A.keys.twb, pr);
-                __syncthreads();
-                br_crt<8>(S, wr >> 2, 8 * (wr & 3), lane);
+                crt_rows<8>(S.acc[wr >> 2], X.xch[(wr >> 2) * 2 + 0], X.xch[(wr >> 2) * 2 + 1],
+                            8 * (wr & 3), lane);
                 __syncthreads();
             }
         }
@@ -1139,10 +1156,11 @@ cudaError_t launch_bk_to_ntt(const int32_t *bk_dev, uint32_t *bk_ntt, int n, con
 // Dynamic shared memory of a shape: B bootstraps, plus the key stages for
 // the staged shape and its control (which reserves them unused, so both run
 // one CTA per SM).
-template <int B, int STAGE>
+template <int B, int STAGE, int W = 4>
 constexpr size_t br_smem(bool stage_room)
 {
-    return B * sizeof(BrSmem) + (STAGE || stage_room ? sizeof(BkStage) : 0);
+    return B * sizeof(BrSmem) + (STAGE || stage_room ? sizeof(BkStage) : 0) +
+           (W == 8 ? sizeof(SplitExtra) : 0);
 }
 
 template <int B, int W, int STAGE = 0, int MINB = 0>
@@ -1162,10 +1180,10 @@ static int br_blocks(int dev, bool stage_room = false)
     static int cached[2][64] = {{0}};
     if (dev < 0 || dev >= 64)
         return 1;
-    const size_t smem = br_smem<B, STAGE>(stage_room);
+    const size_t smem = br_smem<B, STAGE, W>(stage_room);
     if (!cached[stage_room][dev]) {
         // the attribute covers the larger of the two requests of the shape
-        br_prepare<B, W, STAGE, MINB>(br_smem<B, STAGE>(B == 2 && W == 4));
+        br_prepare<B, W, STAGE, MINB>(br_smem<B, STAGE, W>(B == 2 && W == 4));
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<B, W, STAGE, MINB>,
                                                           32 * W * B, smem) != cudaSuccess) {
@@ -1288,10 +1306,12 @@ cudaError_t launch_blind_rotate(const DevKeys &keys, const uint8_t *ops, const i
         k_blind_rotate<2, 4><<<blocks, 256, br_smem<2, 0>(true), stream>>>(A);
         break;
     case kBrSplitStaged:
-        k_blind_rotate<1, 8, 1><<<blocks, 256, br_smem<1, 1>(false), stream>>>(A);
+        k_blind_rotate<1, 8, 1><<<blocks, 256, br_smem<1, 1, 8>(false), stream>>>(A);
         break;
     case kBrFive: k_blind_rotate<1, 4, 0, 5><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
-    case kBrSplit: k_blind_rotate<1, 8><<<blocks, 256, sizeof(BrSmem), stream>>>(A); break;
+    case kBrSplit:
+        k_blind_rotate<1, 8><<<blocks, 256, br_smem<1, 0, 8>(false), stream>>>(A);
+        break;
     default: k_blind_rotate<1, 4><<<blocks, 128, sizeof(BrSmem), stream>>>(A); break;
     }
     return cudaGetLastError();
