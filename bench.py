@@ -621,6 +621,8 @@ def run_serve(args):
                          d(kd.ksk_noise))
     ctx = api.Context(p)
     ctx.set_keys(bk, ksk)
+    # launch shapes and the level times the serving loop's iteration choice uses
+    ctx.autotune(args.tune_cache)
     s_dev = d(kd.s)
     variants = 8
     inputs = {}   # per kind: (A, B, plaintexts) with `variants` distinct operands

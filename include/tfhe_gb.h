@@ -402,9 +402,11 @@ typedef struct {
  * The pool is one reserved range of device addresses mapped in steps
  * (driver virtual memory management); where that is unavailable it is one
  * fixed allocation of the cap (or of half the free memory, at most 32 GB).  Each iteration runs the
- * next level of every admitted request as one batched bootstrap, up to
- * max_batch_gates gates (0: a default of 8 waves of the GPU); requests that
- * arrive meanwhile join the next iteration.  While serving, the context
+ * next level of admitted requests as one batched bootstrap, up to
+ * max_batch_gates gates (0: a default of 8 waves of the GPU), chosen as
+ * tfhe_serve_select describes with the autotuner's level times (call
+ * tfhe_ctx_autotune first; untuned, a fixed model); requests that arrive
+ * meanwhile join the next iteration.  While serving, the context
  * must not be used for other evaluation calls.  The paper's GPU framework
  * evaluates one circuit at a time; this is its level batching (section
  * V-A) extended across requests. */
@@ -426,6 +428,29 @@ int tfhe_serve_stats(tfhe_ctx *ctx, tfhe_serve_info *out);
 /* Latencies (ms) of completed requests in completion order; *count gets the
  * total, at most cap are copied. */
 int tfhe_serve_latencies(tfhe_ctx *ctx, double *ms, size_t cap, size_t *count);
+
+/* Host-only: the choice each serving iteration makes (no counterpart in the
+ * paper, which evaluates one circuit at a time; needs no context and no
+ * GPU).  Inputs, one entry per admitted request in admission order:
+ * width[i] > 0 the gates of its next level, remaining[i] > 0 its levels
+ * left (that one included), waited[i] >= 0 the iterations run since its
+ * last level ran.  Requests are ranked by remaining + waited, descending,
+ * ties in admission order; in that order each next level is taken while
+ * the running total stays within cap gates (a level that does not fit is
+ * passed over; the first is always taken).  Of that list the prefix with
+ * the most gates per estimated millisecond is kept, the longest on ties.
+ * The estimate for g gates: while g <= 4 num_sms, level_ms[bucket of g]
+ * (the autotuner's 8 level times for widths up to 152, 304, 608, 1216,
+ * 2432, 4864, 9728 gates and more) when wave_ms > 0 and that entry is
+ * > 0, else 0.35, 0.55 or 1 times wave_ms (1 when wave_ms is 0) for g up to
+ * num_sms, 2 num_sms or 4 num_sms; above, ceil(g / (4 num_sms)) wave_ms.
+ * level_ms may be NULL.  taken (n entries, caller-owned) receives the
+ * indices of the requests kept, in rank order; *ntaken their number.
+ * TFHE_EINVAL on a null pointer where n > 0, num_sms or cap <= 0, or an
+ * entry out of range. */
+int tfhe_serve_select(const int64_t *width, const int32_t *remaining, const int32_t *waited,
+                      size_t n, int64_t cap, int32_t num_sms, const float *level_ms,
+                      float wave_ms, int32_t *taken, size_t *ntaken);
 
 /* Drain queued and in-flight requests, stop the worker, free the pool.
  * Returns TFHE_OK or the error that stopped serving. */

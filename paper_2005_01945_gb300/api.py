@@ -101,6 +101,10 @@ EXPORTS = {
     "tfhe_serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tfhe_serve_latencies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "tfhe_serve_select": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_int64,
+                                                               ctypes.c_int32, ctypes.c_void_p,
+                                                               ctypes.c_float, ctypes.c_void_p,
+                                                               ctypes.POINTER(ctypes.c_size_t)]),
     "tfhe_serve_stop": (ctypes.c_int, [ctypes.c_void_p]),
     "tfhe_keygen": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 9),
     "tfhe_encrypt_bits": (ctypes.c_int, [ctypes.POINTER(CParams)] + [ctypes.c_void_p] * 5
@@ -460,6 +464,27 @@ def schedule_info(jobs, policy=1, target=0):
                                     ctypes.c_void_p(widths.ctypes.data), depth.value,
                                     ctypes.byref(depth), ctypes.byref(gates)))
     return widths[:depth.value], int(gates.value)
+
+
+def serve_select(width, remaining, waited, cap, num_sms, level_ms=None, wave_ms=0.0):
+    """Host-only: indices of the requests one serving iteration takes, in
+    rank order (tfhe_serve_select; no GPU needed)."""
+    w = np.ascontiguousarray(width, dtype=np.int64)
+    r = np.ascontiguousarray(remaining, dtype=np.int32)
+    t = np.ascontiguousarray(waited, dtype=np.int32)
+    if not (len(w) == len(r) == len(t)):
+        raise ValueError("width, remaining and waited differ in length")
+    lm = None if level_ms is None else np.ascontiguousarray(level_ms, dtype=np.float32)
+    if lm is not None and lm.shape != (8,):
+        raise ValueError("level_ms holds 8 bucket times")
+    out = np.zeros(max(len(w), 1), dtype=np.int32)
+    nt = ctypes.c_size_t(0)
+    _check(lib().tfhe_serve_select(
+        ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(r.ctypes.data),
+        ctypes.c_void_p(t.ctypes.data), len(w), cap, num_sms,
+        None if lm is None else ctypes.c_void_p(lm.ctypes.data), wave_ms,
+        ctypes.c_void_p(out.ctypes.data), ctypes.byref(nt)))
+    return out[:nt.value].copy()
 
 
 def tc_key_bytes() -> int:

@@ -7,7 +7,8 @@
 // the device's free HBM (under the caller's cap) when they do not, copies
 // their inputs in, and then runs iterations: one iteration is one batched
 // blind-rotation launch plus one key-switch launch over the next level of
-// every admitted request (oldest first, up to a gate cap).  A request's
+// admitted requests, chosen by serve_select (deepest first, up to a gate
+// cap, trimmed to the width that runs most gates per unit of time).  A request's
 // level k+1 is enqueued right behind level k on the same stream, so the
 // worker keeps two iterations in flight and the device never waits for the
 // host; requests admitted meanwhile join the next iteration.  When a
@@ -26,6 +27,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -291,6 +293,7 @@ struct SrvReq {
     std::shared_ptr<const Netlist> nl;
     long rows0 = 0, rows1 = 0, inst_rows = 0, base = -1;
     int next_level = 1;
+    int waited = 0;                // iterations run since this request's last level ran
     int state = 0;                 // 0 queued, 1 admitted, 2 done, < 0 error code
     double t_submit = 0, t_done = 0;
     std::vector<long> level_start; // gates sorted by level: [level_start[l-1], level_start[l])
@@ -334,6 +337,59 @@ struct Server {
     double t_first_submit = -1, t_last_done = 0;
     int wait_limit_ms = 120000;
 };
+
+// Estimated device time (ms) of one serving iteration of n gates: the
+// autotuner's measured level time of n's width bucket while n fits one wave
+// of 4 bootstraps per SM, whole waves above.  Untuned (wave_ms 0) in units
+// of one wave, with the ratios measured on GB300: a level of at most one
+// bootstrap per SM takes 0.35 of a full wave, of at most two per SM 0.55.
+static double iter_cost(long n, int num_sms, const float *level_ms, float wave_ms)
+{
+    const long w4 = 4L * num_sms;
+    const double t4 = wave_ms > 0.f ? wave_ms : 1.0;
+    if (n > w4)
+        return (double)((n + w4 - 1) / w4) * t4;
+    if (level_ms && wave_ms > 0.f && level_ms[tune_bucket(n)] > 0.f)
+        return level_ms[tune_bucket(n)];
+    return n <= num_sms ? 0.35 * t4 : (n <= 2L * num_sms ? 0.55 * t4 : t4);
+}
+
+// The requests one iteration takes, as indices into the running list
+// (taken[0 .. return value)).  Requests are ranked by the levels they have
+// left plus the iterations they have waited since their last level ran
+// (the deepest ones bound when the work ends; waiting raises a shallow
+// request's rank so that it is not starved), ties in admission order.  In
+// rank order each request's next level is taken while the gate cap allows
+// (a level that does not fit is passed over; the first is always taken).
+// Of that list the prefix with the most gates per estimated unit of device
+// time is kept (the longest on ties): an iteration that would spill a few
+// gates into another wave, or past the width of a narrow level, leaves its
+// lowest-ranked requests for the next one.  Host-only and deterministic.
+long serve_select(long n, const long *width, const int *remaining, const int *waited, long cap,
+                  int num_sms, const float *level_ms, float wave_ms, int32_t *taken)
+{
+    std::vector<int32_t> rank((size_t)n);
+    std::iota(rank.begin(), rank.end(), 0);
+    std::stable_sort(rank.begin(), rank.end(), [&](int32_t x, int32_t y) {
+        return (long)remaining[x] + waited[x] > (long)remaining[y] + waited[y];
+    });
+    long k = 0, count = 0;
+    for (int32_t i : rank) {
+        if (k > 0 && count + width[i] > cap)
+            continue;
+        taken[k++] = i;
+        count += width[i];
+    }
+    long keep = 0, c = 0;
+    double best = -1.0;
+    for (long j = 0; j < k; ++j) {
+        c += width[taken[j]];
+        const double rate = (double)c / iter_cost(c, num_sms, level_ms, wave_ms);
+        if (rate >= best)
+            best = rate, keep = j + 1;
+    }
+    return keep;
+}
 
 static int srv_fail_all(Server &S, int code)
 {
@@ -482,18 +538,26 @@ static void srv_loop(Server *Sp)
             srv_fail_all(S, rc);
             return;
         }
-        std::vector<SrvReq *> take, rest, finishing;
+        std::vector<SrvReq *> take, finishing;
         long count = 0, nout = 0;
         {
             std::lock_guard<std::mutex> lock(S.mu);
-            for (SrvReq *r : S.running) {
-                const long w = r->level_start[r->next_level] - r->level_start[r->next_level - 1];
-                if (!take.empty() && count + w > S.max_batch) {
-                    rest.push_back(r);
-                    continue;
-                }
-                take.push_back(r);
-                count += w;
+            const long nr = (long)S.running.size();
+            std::vector<long> wv((size_t)nr);
+            std::vector<int> rem((size_t)nr), wt((size_t)nr);
+            std::vector<int32_t> tk((size_t)nr);
+            for (long i = 0; i < nr; ++i) {
+                const SrvReq *r = S.running[i];
+                wv[i] = r->level_start[r->next_level] - r->level_start[r->next_level - 1];
+                rem[i] = r->nl->depth - r->next_level + 1;
+                wt[i] = r->waited;
+            }
+            const long nt = serve_select(nr, wv.data(), rem.data(), wt.data(), S.max_batch,
+                                         ctx->num_sms, ctx->keys.tune_ms, ctx->keys.wave_ms[0],
+                                         tk.data());
+            for (long j = 0; j < nt; ++j) {
+                take.push_back(S.running[tk[j]]);
+                count += wv[tk[j]];
             }
         }
         if (take.empty()) {
@@ -581,8 +645,12 @@ static void srv_loop(Server *Sp)
                              (long)finishing.size();
             S.stats.gates += count;
             S.stats.iterations++;
-            for (SrvReq *r : take)
+            for (SrvReq *r : S.running)
+                r->waited++;
+            for (SrvReq *r : take) {
                 r->next_level++;
+                r->waited = 0;
+            }
             S.running.erase(std::remove_if(S.running.begin(), S.running.end(),
                                            [](SrvReq *r) { return r->next_level > r->nl->depth; }),
                             S.running.end());
@@ -791,6 +859,27 @@ int tfhe_serve_latencies(tfhe_ctx *ctx, double *ms, size_t cap, size_t *count)
     *count = S->latencies.size();
     if (ms)
         std::memcpy(ms, S->latencies.data(), std::min(cap, S->latencies.size()) * sizeof(double));
+    return TFHE_OK;
+}
+
+int tfhe_serve_select(const int64_t *width, const int32_t *remaining, const int32_t *waited,
+                      size_t n, int64_t cap, int32_t num_sms, const float *level_ms,
+                      float wave_ms, int32_t *taken, size_t *ntaken)
+{
+    if (!ntaken || num_sms <= 0 || cap <= 0 || (n && (!width || !remaining || !waited || !taken)))
+        return TFHE_EINVAL;
+    std::vector<long> w(n);
+    std::vector<int> rem(n), wt(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (width[i] <= 0 || remaining[i] <= 0 || waited[i] < 0)
+            return TFHE_EINVAL;
+        w[i] = (long)width[i];
+        rem[i] = remaining[i];
+        wt[i] = waited[i];
+    }
+    *ntaken = n ? (size_t)serve_select((long)n, w.data(), rem.data(), wt.data(), (long)cap,
+                                       num_sms, level_ms, wave_ms, taken)
+                : 0;
     return TFHE_OK;
 }
 
