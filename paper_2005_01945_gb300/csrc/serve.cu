@@ -531,7 +531,7 @@ static void srv_loop(Server *Sp)
                 return;
             }
         }
-        // build the iteration: next level of running requests, oldest first
+        // build the iteration: next levels of running requests (serve_select)
         Iter &I = S.it[S.seq & 1];
         int rc = srv_wait(S, I);
         if (rc != TFHE_OK) {
@@ -605,7 +605,7 @@ static void srv_loop(Server *Sp)
         for (SrvReq *r : finishing)
             for (int32_t w : r->nl->out)
                 I.h_out[o++] = (int32_t)(r->base + w);
-        NvtxRange range("tfhe: serving iteration (one level of every admitted request)");
+        NvtxRange range("tfhe: serving iteration (one level of each selected request)");
         cudaError_t e = cudaMemcpyAsync(I.d_ops, I.h_ops, count, cudaMemcpyHostToDevice, S.st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(I.d_idx, I.h_idx, 4 * icap * sizeof(int32_t),
