@@ -103,6 +103,9 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson requests at 3 rates (config 4)")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-sample", type=int, default=400,
+                    help="requests per arrival rate of the bounded config-4 serving measurement "
+                         "in the bench line (0: skip)")
     ap.add_argument("--serve-circuits", default="paper", choices=["paper", "shallow"],
                     help="serving circuits: the paper's ripple-carry adders and shift-and-add "
                          "multipliers, or parallel-prefix adders and Dadda-tree multipliers "
@@ -603,27 +606,15 @@ SERVE_KINDS_SHALLOW = [("gate", 0, 1), ("add16", 10, 16), ("add32", 10, 32), ("m
                        ("mul32", 11, 32)]
 
 
-def run_serve(args):
-    """Config 4: a Poisson request stream at 0.3, 0.6 and 0.9 of the measured
-    saturated request rate, requests drawn uniformly from {single gate,
-    16-bit add, 32-bit add, 16-bit mul, 32-bit mul}; keys device-resident,
-    admission by free device memory (the ciphertext pool grows from free HBM),
-    gates batched across requests per level."""
+def measure_serving(ctx, p, s_dev, d, seed, table, per_rate, burst=200):
+    """Config 4 on a context whose keys are set: the saturated capacity from a
+    burst of `burst` requests, then `per_rate` requests as a Poisson stream at
+    0.3, 0.6 and 0.9 of it; requests drawn uniformly from `table`, admission
+    by free device memory (the ciphertext pool grows from free HBM), gates
+    batched across requests per level.  Every add32 and mul32 result is
+    checked by decryption.  -> (capacity dict, per-rate list)."""
     import torch
-    from paper_2005_01945_gb300 import api, build, synth
-    build.build()
-    table = SERVE_KINDS_SHALLOW if args.serve_circuits == "shallow" else SERVE_KINDS
-    p = synth.TFHEParams()
-    seed = synth.MASTER_SEED + 4
-    kd = synth.key_draws(p, seed)
-    d = api.to_device
-    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
-                         d(kd.ksk_noise))
-    ctx = api.Context(p)
-    ctx.set_keys(bk, ksk)
-    # launch shapes and the level times the serving loop's iteration choice uses
-    ctx.autotune(args.tune_cache)
-    s_dev = d(kd.s)
+    from paper_2005_01945_gb300 import api, synth
     variants = 8
     inputs = {}   # per kind: (A, B, plaintexts) with `variants` distinct operands
     for name, kind, w in table:
@@ -635,11 +626,11 @@ def run_serve(args):
                         api.encrypt_bits(p, s_dev, d(cb.mask), d(cb.noise), d(bb)), a, b)
     gates_of = {name: (1 if kind == 0 else api.circuit_info(kind, w)[0])
                 for name, kind, w in table}
+    dev = s_dev.device
 
     def run_stream(arrivals, kinds, budget=0):   # 0: the pool grows from free HBM
-        n = len(arrivals)
         outs = {name: torch.empty((max(1, int((kinds == k).sum())), w, api.LWE_STRIDE),
-                                  dtype=torch.int32, device="cuda")
+                                  dtype=torch.int32, device=dev)
                 for k, (name, kind, w) in enumerate(table)}
         used = {name: 0 for name, _, _ in table}
         ctx.serve_start(budget)
@@ -661,7 +652,7 @@ def run_serve(args):
         stats = ctx.serve_stats()
         ctx.serve_stop()
         torch.cuda.synchronize()
-        # verify the multiplications of the stream by decryption
+        # verify the multiplications and additions of the stream by decryption
         ok = True
         for name in ("mul32", "add32"):
             _, _, a, b = inputs[name]
@@ -678,14 +669,14 @@ def run_serve(args):
 
     # saturated capacity: a burst of requests all at once
     rng = np.random.default_rng(seed)
-    burst = 200
     kinds = rng.integers(0, len(table), size=burst)
-    lats, stats, wall, ok, _ = run_stream(np.zeros(burst), kinds)
+    _, stats, wall, ok_cap, _ = run_stream(np.zeros(burst), kinds)
     cap_gates = stats["gates"] / wall
     mean_gates = float(np.mean([gates_of[n] for n, _, _ in table]))
     cap_req = cap_gates / mean_gates
+    capacity = {"burst_requests": burst, "gates_per_s": cap_gates, "req_per_s": cap_req,
+                "mean_gates_per_request": mean_gates, "verified": ok_cap}
     results = []
-    per_rate = args.serve_requests // 3
     for frac in (0.3, 0.6, 0.9):
         lam = frac * cap_req
         arr = np.cumsum(rng.exponential(1.0 / lam, size=per_rate))
@@ -702,13 +693,38 @@ def run_serve(args):
                         "mul32_p50_ms": float(np.percentile(m32, 50)) if len(m32) else None,
                         "mul32_p99_ms": float(np.percentile(m32, 99)) if len(m32) else None,
                         "verified": ok})
+    return capacity, results
+
+
+def run_serve(args):
+    """Config 4: a Poisson request stream at 0.3, 0.6 and 0.9 of the measured
+    saturated request rate, requests drawn uniformly from {single gate,
+    16-bit add, 32-bit add, 16-bit mul, 32-bit mul}; keys device-resident,
+    admission by free device memory (the ciphertext pool grows from free HBM),
+    gates batched across requests per level."""
+    from paper_2005_01945_gb300 import api, build, synth
+    build.build()
+    table = SERVE_KINDS_SHALLOW if args.serve_circuits == "shallow" else SERVE_KINDS
+    p = synth.TFHEParams()
+    seed = synth.MASTER_SEED + 4
+    kd = synth.key_draws(p, seed)
+    d = api.to_device
+    bk, ksk = api.keygen(p, d(kd.s), d(kd.S), d(kd.bk_mask), d(kd.bk_noise), d(kd.ksk_mask),
+                         d(kd.ksk_noise))
+    ctx = api.Context(p)
+    ctx.set_keys(bk, ksk)
+    # launch shapes and the level times the serving loop's iteration choice uses
+    ctx.autotune(args.tune_cache)
+    capacity, results = measure_serving(ctx, p, d(kd.s), d, seed, table,
+                                        args.serve_requests // 3)
     print(json.dumps({"metric": "serving: p50/p99 request latency and gates/s under Poisson load",
                       "config": {"workload": "config 4: requests uniform over {XOR gate, add16, "
                                              "add32, mul16, mul32}; mean "
-                                             f"{mean_gates:.1f} gates/request",
+                                             f"{capacity['mean_gates_per_request']:.1f} "
+                                             "gates/request",
                                  "circuits": args.serve_circuits,
-                                 "capacity_gates_per_s": cap_gates,
-                                 "capacity_req_per_s": cap_req},
+                                 "capacity_gates_per_s": capacity["gates_per_s"],
+                                 "capacity_req_per_s": capacity["req_per_s"]},
                       "rates": results}), flush=True)
     ctx.close()
 
@@ -1023,6 +1039,19 @@ def main():
         product_choice = {k: v for k, v in product_choice.items()
                           if k not in ("tc_prepare_key_ms", "tc_products_ms", "ntt_blind_rotation_ms")}
 
+    # ---- config 4 (bounded): serving capacity and a Poisson stream of
+    # args.serve_sample requests at each of 0.3, 0.6 and 0.9 of it, same keys
+    # and tuned shapes; `python bench.py --serve` runs the 10,000-request form
+    serving = None
+    if rank == 0 and args.serve_sample > 0:
+        capacity, rates = measure_serving(ctx, p, s_dev, d, seed + 4, SERVE_KINDS,
+                                          args.serve_sample)
+        serving = {"workload": "config 4: requests uniform over {XOR gate, add16, add32, "
+                               "mul16, mul32} (ripple-carry adders, shift-and-add "
+                               "multipliers), admission by free HBM",
+                   "requests_per_rate": args.serve_sample, "capacity": capacity,
+                   "rates": rates}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
         sample = OracleSample(args.cpu_gates, seed)
@@ -1059,7 +1088,8 @@ def main():
                 "keyswitch": keyswitch,
                 "cpu_baseline": cpu, "configs": configs, "product_choice": product_choice,
                 "mul32_latency": latency,
-                "mul32_shallow_latency": latency_tree, "verified": verified}
+                "mul32_shallow_latency": latency_tree, "serving": serving,
+                "verified": verified}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
