@@ -323,6 +323,98 @@ __device__ __forceinline__ void inv_ntt(uint32_t (&x)[32], uint32_t *sbuf, int l
     gs32<false>(x, pr);
 }
 
+// The inverse transform shared by two warps of one sub-partition (the
+// 8-warp shapes): warp K holds registers 16K .. 16K + 15 of every lane.  In
+// each 32-point Gentleman-Sande pass the butterflies of distance 1 .. 8 stay
+// inside a warp's registers; the last stage (distance 16) pairs register j
+// with j + 16, so each warp publishes its reduced inputs of that stage in
+// `ex` ([32 registers][32 lanes]) and reads its partner's after a barrier
+// of the two warps (named barrier `bar`).  Every butterfly, twiddle and
+// reduction is the one gs32 / inv_ntt performs, so the result is identical.
+__device__ __forceinline__ void pair_sync(int bar)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory");
+}
+
+template <bool CYC, int K>
+__device__ __forceinline__ void gs32_half(uint32_t (&x)[32], const Prime &pr, uint32_t *ex,
+                                          int lane, int bar)
+{
+    constexpr LazyPlan PL = CYC ? kPlanInvD : kPlanInvA;
+    const uint32_t(*tb)[32][2] = CYC ? c_ntt.izd : c_ntt.iza;
+#pragma unroll
+    for (int s = 4; s >= 1; --s) {
+        const int m = 1 << s, ln = 16 >> s;
+#pragma unroll
+        for (int g = 0; g < m; ++g) {
+            const uint32_t w = tb[pr.P][m + g][0];
+            const uint32_t wp = tb[pr.P][m + g][1];
+#pragma unroll
+            for (int jj = 0; jj < ln; ++jj) {
+                const int j = 2 * g * ln + jj;
+                if ((j >> 4) != K)
+                    continue;
+                const LazyStep &L = PL.st[s][g * ln + jj];
+                const uint32_t u = lazy_reduce_n(x[j], L.ru, L.nru, pr);
+                const uint32_t v = lazy_reduce_n(x[j + ln], L.rv, L.nrv, pr);
+                x[j] = u + v;
+                const uint32_t d = u - v + pr.kq(L.off);
+                x[j + ln] = (CYC && g == 0) ? d : mul_shoup(d, w, wp, pr.q);
+            }
+        }
+    }
+    // distance 16: warp 0 holds the u, warp 1 the v of every butterfly
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+        const LazyStep &L = PL.st[0][jj];
+        const int r = 16 * K + jj;
+        x[r] = K == 0 ? lazy_reduce_n(x[r], L.ru, L.nru, pr) : lazy_reduce_n(x[r], L.rv, L.nrv, pr);
+        ex[r * 32 + lane] = x[r];
+    }
+    pair_sync(bar);
+    const uint32_t w = tb[pr.P][1][0], wp = tb[pr.P][1][1];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+        const LazyStep &L = PL.st[0][jj];
+        const int r = 16 * K + jj;
+        const uint32_t other = ex[(16 * (1 - K) + jj) * 32 + lane];
+        if (K == 0) {
+            x[r] = x[r] + other;
+        } else {
+            const uint32_t d = other - x[r] + pr.kq(L.off);
+            x[r] = CYC ? d : mul_shoup(d, w, wp, pr.q);
+        }
+        x[r] = lazy_reduce_n(x[r], PL.fin[r], PL.nfin[r], pr);
+    }
+}
+
+// inv_ntt on two warps (see gs32_half): same input layout restricted to
+// registers 16K .. 16K + 15, same output layout and values.  sbuf: the
+// pair's transpose scratch (kSlot words).
+template <int K>
+__device__ __forceinline__ void inv_ntt_half(uint32_t (&x)[32], uint32_t *sbuf, uint32_t *ex,
+                                             int lane, int lane_brv,
+                                             const uint2 *__restrict__ twb, const Prime &pr,
+                                             int bar)
+{
+    gs32_half<true, K>(x, pr, ex, lane, bar);
+    const uint2 *tw = twb + (pr.P * 2 + 1) * 1024 + lane;
+#pragma unroll
+    for (int r = 16 * K; r < 16 * K + 16; ++r) {
+        const uint2 t = __ldg(tw + r * 32);
+        x[r] = mul_shoup(x[r], t.x, t.y, pr.q);
+    }
+    uint32_t *wr = sbuf + lane_brv, *rd = sbuf + lane * 33;
+#pragma unroll
+    for (int r = 16 * K; r < 16 * K + 16; ++r)
+        wr[r * 33] = x[r];             // lane k1, i1 = r -> slot[i1][brv5(k1)]
+    pair_sync(bar);
+#pragma unroll
+    for (int r = 16 * K; r < 16 * K + 16; ++r)
+        x[r] = rd[r];                  // lane i1 reads slot[i1][r]
+    gs32_half<false, K>(x, pr, ex, lane, bar);
+}
+
 // ---------------------------------------------------------------------
 // Bootstrapping key -> NTT domain
 // ---------------------------------------------------------------------
@@ -395,14 +487,16 @@ struct BkStage {
 };
 constexpr uint32_t kBkStepBytes = 4 * kN * sizeof(uint4);   // 64 KB
 
-// The 8-warp shape's own transpose scratch and residue rows for its
-// inverse transforms (one bootstrap per CTA leaves the room), so that the
-// four warps go from their pointwise products straight into their inverse
-// transform without waiting for the others to finish reading the digit
-// transforms.
+// The 8-warp shape's own transpose scratch, exchange rows and residue rows
+// for its inverse transforms (one bootstrap per CTA leaves the room), so
+// that the warps go from their pointwise products straight into their
+// inverse transform without waiting for the others to finish reading the
+// digit transforms.  Warps w and w + 4 (one sub-partition) share the
+// pointwise products and inverse transform of (p, h) = (w >> 1, w & 1).
 struct SplitExtra {
-    uint32_t scratch[4][kSlot];  // transpose scratch of warp (p, h)
+    uint32_t scratch[4][kSlot];  // transpose scratch of the warps of (p, h)
     uint32_t xch[4][kN];         // residues [p * 2 + h][reg*32+lane], [0, q)
+    uint32_t ex[4][kN];          // last-stage exchange of the two warps of (p, h)
 };
 constexpr long kBkSpin = 1L << 20;                           // x ~1 us per try
 
@@ -516,7 +610,9 @@ __device__ __forceinline__ void br_digit_fwd(uint32_t (&x)[32], BrSmem &S, int c
 }
 
 // Phase 2: pointwise products for output polynomial p modulo prime h,
-// summed over the 4 digit rows; result in [0, 2q).
+// summed over the 4 digit rows; result in [0, 2q).  Registers R0 .. R0 +
+// NR - 1 (all 32 unless two warps share the polynomial).
+template <int R0 = 0, int NR = 32>
 __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
                                              const uint4 *__restrict__ bkp, int lane,
                                              const Prime &pr)
@@ -525,7 +621,7 @@ __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
     const uint32_t *f0 = S.fwd[0][pr.P], *f1 = S.fwd[1][pr.P], *f2 = S.fwd[2][pr.P],
                    *f3 = S.fwd[3][pr.P];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = R0; r < R0 + NR; ++r) {
         const uint4 b = __ldg(bkp + r * 32 + lane);
         const int e = r * 32 + lane;
         uint64_t s = (uint64_t)f0[e] * b.x;
@@ -536,7 +632,9 @@ __device__ __forceinline__ void br_pointwise(uint32_t (&x)[32], const BrSmem &S,
     }
 }
 
-// Phase 2 with the key staged in shared memory (shape kBrStaged).
+// Phase 2 with the key staged in shared memory (shapes kBrStaged,
+// kBrSplitStaged).
+template <int R0 = 0, int NR = 32>
 __device__ __forceinline__ void br_pointwise_staged(uint32_t (&x)[32], const BrSmem &S,
                                                     const uint4 *bks, int lane, const Prime &pr)
 {
@@ -545,7 +643,7 @@ __device__ __forceinline__ void br_pointwise_staged(uint32_t (&x)[32], const BrS
                    *f3 = S.fwd[3][pr.P];
     const uint32_t base = br_saddr(bks);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = R0; r < R0 + NR; ++r) {
         const int e = r * 32 + lane;
         uint4 b;
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -570,6 +668,29 @@ __device__ __forceinline__ void br_inverse(uint32_t (&x)[32], BrSmem &S, int w4,
 #pragma unroll
     for (int r = 0; r < 32; ++r)
         xch[r * 32 + lane] = csub(x[r], pr.q);
+}
+
+// Phases 2 and 3 of the 8-warp shapes: warp K of the pair (w4, w4 + 4)
+// takes registers 16K .. 16K + 15 of the pointwise products of (p, h) and
+// of its inverse transform (named barrier 1 + w4), and publishes them
+// reduced to [0, q) in the pair's residue row.
+template <int K>
+__device__ __forceinline__ void split_pointwise_inverse(uint32_t (&x)[32], const BrSmem &S,
+                                                        SplitExtra &X, int w4, bool staged,
+                                                        const uint4 *bks,
+                                                        const uint4 *__restrict__ bki, int lane,
+                                                        int lane_brv,
+                                                        const uint2 *__restrict__ twb,
+                                                        const Prime &pr)
+{
+    if (staged)
+        br_pointwise_staged<16 * K, 16>(x, S, bks, lane, pr);
+    else
+        br_pointwise<16 * K, 16>(x, S, bki, lane, pr);
+    inv_ntt_half<K>(x, X.scratch[w4], X.ex[w4], lane, lane_brv, twb, pr, 1 + w4);
+#pragma unroll
+    for (int r = 16 * K; r < 16 * K + 16; ++r)
+        X.xch[w4][r * 32 + lane] = csub(x[r], pr.q);
 }
 
 // Phase 4: CRT of (r0 mod q0, r1 mod q1) to the centred integer, mod 2^32,
@@ -810,26 +931,25 @@ __global__ void __launch_bounds__(32 * W * B,
             } else {
                 br_digit_fwd(x, S, wr >> 2, (wr >> 1) & 1, a, lane, A.keys.twb, pr);
                 __syncthreads();
-                if (wr < 4) {
-                    bool staged = false;
-                    if (STAGE) {
-                        staged = !G.abort && bk_wait(&G.full[u & 1], (u >> 1) & 1);
-                        if (!staged && !G.abort) {
-                            G.abort = 1;   // read this and later steps from global memory
-                            atomicOr(A.status, kErrTimeout);
-                        }
+                bool staged = false;
+                if (STAGE) {
+                    staged = !G.abort && bk_wait(&G.full[u & 1], (u >> 1) & 1);
+                    if (!staged && !G.abort) {
+                        G.abort = 1;   // read this and later steps from global memory
+                        atomicOr(A.status, kErrTimeout);
                     }
-                    if (staged)
-                        br_pointwise_staged(x, S, &G.bk[u & 1][p * 2 + h][0], lane, pr);
-                    else
-                        br_pointwise(x, S, bki, lane, pr);
-                    // straight on: the inverse writes only this warp's own
-                    // scratch and residue row
-                    inv_ntt(x, X.scratch[w4], lane, lane_brv, A.keys.twb, pr);
-#pragma unroll
-                    for (int r = 0; r < 32; ++r)
-                        X.xch[w4][r * 32 + lane] = csub(x[r], pr.q);
                 }
+                // warps w and w + 4 each take half the registers of (p, h);
+                // straight on: the inverse writes only the pair's own
+                // scratch, exchange and residue rows
+                if (wr < 4)
+                    split_pointwise_inverse<0>(x, S, X, w4, staged,
+                                               STAGE ? &G.bk[u & 1][p * 2 + h][0] : nullptr, bki,
+                                               lane, lane_brv, A.keys.twb, pr);
+                else
+                    split_pointwise_inverse<1>(x, S, X, w4, staged,
+                                               STAGE ? &G.bk[u & 1][p * 2 + h][0] : nullptr, bki,
+                                               lane, lane_brv, A.keys.twb, pr);
                 __syncthreads();
                 crt_rows<8>(S.acc[wr >> 2], X.xch[(wr >> 2) * 2 + 0], X.xch[(wr >> 2) * 2 + 1],
                             8 * (wr & 3), lane);
