@@ -300,19 +300,22 @@ def test_each_lockstep_group_bit_exact(gpu, orc, group):
     assert np.array_equal(_u32(out)[:, :p.n + 1], want)
 
 
-def test_staged_key_across_groups(gpu, orc):
-    """The key-staging shape on 700 gates: most CTAs run two or more groups
-    of two bootstraps, so the staged buffers and their barriers carry over
-    from group to group.  Every output equals the default shape's, and
-    sampled ones the oracle's."""
+@pytest.mark.parametrize("group", [32, 40, 8])
+def test_staged_key_across_groups(gpu, orc, group):
+    """700 gates on the key-staging shapes (two 4-warp bootstraps per CTA,
+    or one on 8 warps) and on the unstaged 8-warp shape: every CTA runs
+    several groups, so the staged buffers, their mbarriers and the 8-warp
+    shapes' named barriers and exchange rows carry over from group to
+    group.  Every output equals the default shape's, and sampled ones the
+    oracle's."""
     torch, api, p, P = gpu["torch"], gpu["api"], gpu["p"], gpu["P"]
     count = 700
-    bits, cts, dev = _fresh(gpu, orc, count, 91, "stg")
+    bits, cts, dev = _fresh(gpu, orc, count, 91, f"stg{group}")
     ops = ((np.arange(count) * 3) % 6).astype(np.uint8)
     ref = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
     got = torch.zeros((count, 512), dtype=torch.int32, device="cuda")
     gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], ref)
-    gpu["ctx"].set_option(api.OPT_BR_GROUP, 32)
+    gpu["ctx"].set_option(api.OPT_BR_GROUP, group)
     try:
         gpu["ctx"].bootstrap_gates(api.to_device(ops), dev[0], dev[1], got)
     finally:
@@ -320,7 +323,7 @@ def test_staged_key_across_groups(gpu, orc):
     torch.cuda.synchronize()
     assert torch.equal(got, ref)
     assert gpu["ctx"].status() == 0
-    idx = np.array([0, 303, 304, 305, 699])
+    idx = np.array([0, 151, 152, 303, 304, 305, 699])
     want = orc.gates(P, gpu["obk"], gpu["oksk"], ops[idx], cts[0][idx], cts[1][idx])
     assert np.array_equal(_u32(got)[idx, :p.n + 1], want)
 
