@@ -114,6 +114,8 @@ def parse():
                     help="adder / multiplier variants and the compound-gate ablation")
     ap.add_argument("--configs", action="store_true",
                     help="time configs 0 (8 gates), 2 (mul16/mul32 x64) and 3 (matvec 16x16)")
+    ap.add_argument("--config-set", default="0,2,3",
+                    help="with --configs: which of the configs 0, 2 and 3 to run (comma list)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (read if present, appended after tuning)")
     return ap.parse_args()
@@ -562,15 +564,37 @@ def run_configs(args):
         return float(np.median(ms))
 
     dec = lambda t: synth.from_bits(api.decrypt_bits(p, s_dev, t).cpu().numpy())  # noqa: E731
+    chosen = {int(c) for c in args.config_set.split(",") if c.strip()}
+    if not chosen or not chosen <= {0, 2, 3}:
+        raise SystemExit(f"--config-set: expected a comma list of 0, 2, 3, got {args.config_set!r}")
     out = {}
-    # config 0: 8 gates
+    if 0 in chosen:
+        config0(ctx, d, enc, timed, seed, out)
+    if 2 in chosen:
+        config2(ctx, api, enc, timed, dec, seed, out)
+    if 3 in chosen:
+        config3(ctx, api, enc, timed, dec, seed, out)
+    print(json.dumps({"metric": "bootstrapped gates/sec per workload", "unit": "gates/s",
+                      "results": out}), flush=True)
+    ctx.close()
+
+
+def config0(ctx, d, enc, timed, seed, out):
+    """Config 0: 8 gates (NAND, AND, OR, XOR, two each) in one call."""
+    import torch
+    from paper_2005_01945_gb300 import synth
     ops, ba, bb = synth.gates8_inputs(seed)
     A0, B0 = enc(ba, 1, "c0a")[:, 0], enc(bb, 1, "c0b")[:, 0]
     R0 = torch.empty_like(A0)
     ops_d = d(ops)
     ms = timed(lambda: ctx.bootstrap_gates(ops_d, A0, B0, R0), 10)
     out["config0_8gates"] = {"ms": ms, "gates_per_s": 8 / (ms / 1e3)}
-    # config 2: 64 mul16 + 64 mul32 in one schedule
+
+
+def config2(ctx, api, enc, timed, dec, seed, out):
+    """Config 2: 64 mul16 + 64 mul32 in one level schedule."""
+    import torch
+    from paper_2005_01945_gb300 import synth
     a16, b16 = synth.int_pairs(64, 16, seed + 2, "mul16")
     a32, b32 = synth.int_pairs(64, 32, seed + 2, "mul32")
     A16, B16, A32, B32 = enc(a16, 16, "m16a"), enc(b16, 16, "m16b"), enc(a32, 32, "m32a"), \
@@ -584,7 +608,12 @@ def run_configs(args):
               np.array_equal(dec(R32), (a32 * b32) % (1 << 32)))
     out["config2_mul16x64_mul32x64"] = {"ms": ms, "gates": gates,
                                         "gates_per_s": gates / (ms / 1e3), "verified": ok}
-    # config 3: matvec 16x16, 16-bit
+
+
+def config3(ctx, api, enc, timed, dec, seed, out):
+    """Config 3: 16x16 matrix times a length-16 vector, 16-bit words."""
+    import torch
+    from paper_2005_01945_gb300 import synth
     M = synth.random_uints((16, 16), 16, seed + 3, "M")
     v = synth.random_uints(16, 16, seed + 3, "v")
     MM, vv = enc(M, 16, "M"), enc(v, 16, "v")
@@ -594,9 +623,6 @@ def run_configs(args):
     ok = bool(np.array_equal(dec(y), (M * v[None, :]).sum(axis=1) % (1 << 16)))
     out["config3_matvec16"] = {"ms": ms, "gates": gates, "gates_per_s": gates / (ms / 1e3),
                                "verified": ok}
-    print(json.dumps({"metric": "bootstrapped gates/sec per workload", "unit": "gates/s",
-                      "results": out}), flush=True)
-    ctx.close()
 
 
 SERVE_KINDS = [("gate", 0, 1), ("add16", 1, 16), ("add32", 1, 32), ("mul16", 2, 16),
