@@ -10,11 +10,14 @@
 // polynomials each and sums digit_r * BK_i[r] in Z[X]/(X^N + 1) mod 2^32.
 //
 // GB300 design (not the paper's: it used cuFFT in floating point):
-//  * the products are exact: a negacyclic NTT modulo two primes below 2^28
+//  * the products are exact: a negacyclic NTT modulo two primes below 2^27
 //    and a centred CRT lift back to Z/2^32;
 //  * one group of 4 warps owns one bootstrap; a CTA runs B in {1, 2, 4}
 //    bootstraps in lockstep (4B warps) and loops over gate groups
-//    (persistent grid); the accumulators never leave shared memory;
+//    (persistent grid); the accumulators never leave shared memory.  For
+//    narrow levels one bootstrap can instead take 8 warps, or a cluster of
+//    two CTAs (one prime each), and the key of the next CMux step can be
+//    staged in shared memory by bulk copies;
 //  * warp (c, h) of a bootstrap works modulo prime h for the whole CMux:
 //    it forms both digit polynomials of TLWE polynomial c (one rotation)
 //    and transforms them; then, as warp (p, h), it does the pointwise
