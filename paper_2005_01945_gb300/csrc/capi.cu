@@ -1,7 +1,7 @@
 // capi.cu -- extern "C" entry points declared in include/tfhe_gb.h: context
 // and key management, batched gate bootstrapping, its two stages, and the
 // client-side helpers.  Circuit and serving entry points live in
-// circuits.cu and serve.cpp.
+// circuits.cu and serve.cu, the allocation-free gate call in noalloc.cu.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>

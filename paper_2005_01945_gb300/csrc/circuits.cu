@@ -11,13 +11,23 @@
 //  * matvec: y_r = sum_c M[r][c] v[c] (section IV-D) with the products of a
 //    row reduced by tree-based accumulation (section V-B-2): neighbours
 //    (0,1), (2,3), ... are added per level, an odd last term moves up.
+// Variants, each defined gate by gate below: the majority-carry adder (a
+// carry is one 3-input MAJ bootstrap), the number-wise adder GPU_n
+// (section V-B-1), tree-accumulated multiplication (section V-B-2) with
+// ripple or majority-carry adders, full w x w -> 2w products (naive and
+// Karatsuba, section III-B-2), and the low-depth parallel-prefix adder and
+// Dadda-tree multiplier.
 //
-// GB300 design: every gate gets its ASAP level (1 + the deeper input);
-// gates of one level from all instances and all jobs of a batch form one
-// blind-rotation launch and one key-switch launch that gather their inputs
-// from, and scatter their outputs to, a device-resident ciphertext pool.
-// The compiled schedule is cached per job signature and its level
-// sequence is captured once as a CUDA graph and replayed.
+// GB300 design: gates of one level from all instances and all jobs of a
+// batch form one blind-rotation launch and one key-switch launch that
+// gather their inputs from, and scatter their outputs to, a
+// device-resident ciphertext pool.  Levels are ASAP (1 + the deeper
+// input) or, by default, deadline-driven: every gate keeps its ASAP depth
+// bound and levels are filled to whole waves of the GPU (a level unit of
+// 152, 608 or 760 gates, chosen per job mix from the autotuner's measured
+// level and wave times).  The compiled schedule is cached per job
+// signature and its level sequence is captured once as a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <cstring>
 #include <map>

@@ -1,10 +1,14 @@
 // tune.cu -- autotuner for the launch shapes of the two bootstrapping
 // kernels: the blind-rotation CTA shape (1, 2 or 4 bootstraps per CTA in
-// lockstep, one bootstrap spread over 8 warps, or one bootstrap on a
-// cluster of two CTAs) and the key-switch kernel (the tiled kernel with
-// shared-memory key stages, or the direct kernel with its j-split of
-// 1 .. 32 chunks), chosen per level-width bucket by
-// timing the candidates on synthetic ciphertexts with the context's keys.
+// lockstep, two per CTA with the key staged in shared memory, one
+// bootstrap spread over 8 warps with or without the staged key, or one
+// bootstrap on a cluster of two CTAs with or without it) and the
+// key-switch kernel (the tiled kernel with shared-memory key stages, or
+// the direct kernel with its j-split of 1 .. 32 chunks), chosen per
+// level-width bucket by timing the candidates on synthetic ciphertexts
+// with the context's keys.  It also records the time of a level at each
+// bucket's widest width and of one full wave at 4 and at 5 bootstraps per
+// SM, from which the circuit schedules choose their level unit.
 // Results can be cached in a small text file keyed by device name and SM
 // count.  Launch shapes never change results (the arithmetic is exact and
 // order-independent), only time.
