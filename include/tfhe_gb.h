@@ -65,7 +65,8 @@ typedef enum {
     TFHE_ECUDA = -3,    /* CUDA runtime error                            */
     TFHE_ETIMEOUT = -4, /* a bounded device or host wait gave up         */
     TFHE_EBUSY = -5,    /* resource in use (e.g. serving already started) */
-    TFHE_EDEVICE = -6   /* a kernel reported an error in the status word */
+    TFHE_EDEVICE = -6,  /* a kernel reported an error in the status word */
+    TFHE_ECANCELED = -7 /* a served request was cancelled (tfhe_serve_cancel) */
 } tfhe_status;
 
 /* Gate opcodes.  Gate g computes c = (0, mu_g) + alpha_a ca + alpha_b cb
@@ -390,6 +391,7 @@ typedef struct {
                              /* the device's memory)                         */
     uint64_t pool_grows;     /* times admission grew the pool                */
     uint64_t admitted_busy;  /* requests admitted while others were running  */
+    uint64_t cancelled;      /* requests cancelled before they completed      */
 } tfhe_serve_info;
 
 /* Start the request loop on the context's device: a worker thread with its
@@ -422,6 +424,17 @@ int tfhe_serve_poll(tfhe_ctx *ctx, uint64_t id, int *state, double *latency_ms);
 /* Block up to timeout_ms for completion: TFHE_OK, TFHE_ETIMEOUT or the
  * request's failure status. */
 int tfhe_serve_wait(tfhe_ctx *ctx, uint64_t id, int timeout_ms, double *latency_ms);
+
+/* Thread-safe.  Cancel a request that has not completed (no counterpart in
+ * the paper: a serving client that gives up on a request).  A queued
+ * request leaves the queue; an admitted one runs no further level, and the
+ * worker returns its pool rows at its next iteration (every device use of
+ * them is already ordered on the worker's stream ahead of any reuse).  Its
+ * output buffer is never written.  poll and wait then report
+ * TFHE_ECANCELED.  Returns TFHE_OK when cancelled; TFHE_EBUSY when the
+ * request's last level is already on the device (its result will arrive);
+ * TFHE_EINVAL for an unknown id or a request that has completed or failed. */
+int tfhe_serve_cancel(tfhe_ctx *ctx, uint64_t id);
 
 int tfhe_serve_stats(tfhe_ctx *ctx, tfhe_serve_info *out);
 

@@ -25,7 +25,7 @@ NAND, AND, OR, XOR, NOR, XNOR, MAJ, ANDNY, ANDYN, ORNY, ORYN = range(11)
 GATE_NAMES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR", "MAJ", "ANDNY", "ANDYN", "ORNY", "ORYN"]
 
 _STATUS = {0: "TFHE_OK", -1: "TFHE_EINVAL", -2: "TFHE_ENOMEM", -3: "TFHE_ECUDA",
-           -4: "TFHE_ETIMEOUT", -5: "TFHE_EBUSY", -6: "TFHE_EDEVICE"}
+           -4: "TFHE_ETIMEOUT", -5: "TFHE_EBUSY", -6: "TFHE_EDEVICE", -7: "TFHE_ECANCELED"}
 
 
 class TFHEError(RuntimeError):
@@ -98,6 +98,7 @@ EXPORTS = {
                                        ctypes.POINTER(ctypes.c_double)]),
     "tfhe_serve_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]),
+    "tfhe_serve_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "tfhe_serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tfhe_serve_latencies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.POINTER(ctypes.c_size_t)]),
@@ -138,7 +139,7 @@ class CServeInfo(ctypes.Structure):
                                                "iterations", "in_flight", "queued")] + \
                [("wall_ms", ctypes.c_double)] + \
                [(f, ctypes.c_uint64) for f in ("pool_bytes", "pool_cap_bytes", "pool_grows",
-                                               "admitted_busy")]
+                                               "admitted_busy", "cancelled")]
 
 
 _lib = None
@@ -431,6 +432,12 @@ class Context:
         lat = ctypes.c_double(0)
         self._c(lib().tfhe_serve_wait(self._h, rid, int(timeout_ms), ctypes.byref(lat)))
         return float(lat.value)
+
+    def serve_cancel(self, rid):
+        """Cancel a request that has not completed (TFHEError with TFHE_EBUSY
+        when its last level is already on the device, TFHE_EINVAL when it has
+        finished or is unknown)."""
+        self._c(lib().tfhe_serve_cancel(self._h, rid))
 
     def serve_stats(self) -> dict:
         info = CServeInfo()

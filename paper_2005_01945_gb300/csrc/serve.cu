@@ -295,6 +295,8 @@ struct SrvReq {
     int next_level = 1;
     int waited = 0;                // iterations run since this request's last level ran
     int state = 0;                 // 0 queued, 1 admitted, 2 done, < 0 error code
+                                   // (TFHE_ECANCELED: cancelled)
+    bool last_taken = false;       // its last level is in an iteration: too late to cancel
     double t_submit = 0, t_done = 0;
     std::vector<long> level_start; // gates sorted by level: [level_start[l-1], level_start[l])
     std::vector<int32_t> order;    // gate indices sorted by level
@@ -396,7 +398,8 @@ static int srv_fail_all(Server &S, int code)
     std::lock_guard<std::mutex> lock(S.mu);
     S.fatal = code;
     for (SrvReq *r : S.running)
-        r->state = code, r->t_done = now_ms(), S.stats.failed++;
+        if (r->state >= 0)         // not cancelled
+            r->state = code, r->t_done = now_ms(), S.stats.failed++;
     for (SrvReq *r : S.queue)
         r->state = code, r->t_done = now_ms(), S.stats.failed++;
     S.running.clear();
@@ -542,6 +545,18 @@ static void srv_loop(Server *Sp)
         long count = 0, nout = 0;
         {
             std::lock_guard<std::mutex> lock(S.mu);
+            // requests cancelled since they were admitted: their rows go back
+            // to the pool now.  Every device use of those rows (input copies,
+            // levels of in-flight iterations) is already on S.st, ahead of
+            // whatever reuses them, so nothing has to wait.
+            S.running.erase(std::remove_if(S.running.begin(), S.running.end(),
+                                           [&S](SrvReq *r) {
+                                               if (r->state >= 0)
+                                                   return false;
+                                               S.rows.release(r->base, r->inst_rows);
+                                               return true;
+                                           }),
+                            S.running.end());
             const long nr = (long)S.running.size();
             std::vector<long> wv((size_t)nr);
             std::vector<int> rem((size_t)nr), wt((size_t)nr);
@@ -556,7 +571,10 @@ static void srv_loop(Server *Sp)
                                          ctx->num_sms, ctx->keys.tune_ms, ctx->keys.wave_ms[0],
                                          tk.data());
             for (long j = 0; j < nt; ++j) {
-                take.push_back(S.running[tk[j]]);
+                SrvReq *r = S.running[tk[j]];
+                if (r->next_level == r->nl->depth)
+                    r->last_taken = true;   // its output will be gathered
+                take.push_back(r);
                 count += wv[tk[j]];
             }
         }
@@ -837,6 +855,36 @@ int tfhe_serve_wait(tfhe_ctx *ctx, uint64_t id, int timeout_ms, double *latency_
     return TFHE_OK;
 }
 
+int tfhe_serve_cancel(tfhe_ctx *ctx, uint64_t id)
+{
+    if (!ctx || !ctx->server)
+        return TFHE_EINVAL;
+    Server *S = ctx->server;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end())
+        return fail(ctx, TFHE_EINVAL, "unknown request %llu", (unsigned long long)id);
+    SrvReq *r = it->second;
+    if (r->state == 2 || r->state < 0)
+        return fail(ctx, TFHE_EINVAL, "request %llu has already finished",
+                    (unsigned long long)id);
+    if (r->last_taken)
+        return fail(ctx, TFHE_EBUSY, "request %llu: its last level is already on the device",
+                    (unsigned long long)id);
+    if (r->state == 0) {
+        auto q = std::find(S->queue.begin(), S->queue.end(), r);
+        if (q != S->queue.end())
+            S->queue.erase(q);
+    }
+    // an admitted request stays in the worker's running list until its next
+    // iteration drops it and frees its rows
+    r->state = TFHE_ECANCELED;
+    r->t_done = now_ms();
+    S->stats.cancelled++;
+    S->cv.notify_all();
+    return TFHE_OK;
+}
+
 int tfhe_serve_stats(tfhe_ctx *ctx, tfhe_serve_info *out)
 {
     if (!ctx || !out || !ctx->server)
@@ -844,7 +892,8 @@ int tfhe_serve_stats(tfhe_ctx *ctx, tfhe_serve_info *out)
     Server *S = ctx->server;
     std::lock_guard<std::mutex> lock(S->mu);
     *out = S->stats;
-    out->in_flight = (uint64_t)S->running.size();
+    out->in_flight = (uint64_t)std::count_if(S->running.begin(), S->running.end(),
+                                             [](const SrvReq *r) { return r->state >= 0; });
     out->queued = (uint64_t)S->queue.size();
     out->wall_ms = S->t_first_submit < 0 ? 0.0 : S->t_last_done - S->t_first_submit;
     return TFHE_OK;

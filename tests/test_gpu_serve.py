@@ -197,6 +197,73 @@ def test_wait_timeout_then_result(env):
         ctx.close()
 
 
+def _one_request(env, kind, w, seed):
+    """One request of `kind` (opcode `w` for a gate, else the bit width) on
+    uniform random operands, encrypted on the device and on the host."""
+    api, p, P, kd, orc = env["api"], env["p"], env["P"], env["kd"], __import__("oracle")
+    d = api.to_device
+    s_dev = d(kd.s)
+    nb = 1 if kind == api.GATE else w
+    bits = [synth.random_bits((nb,), seed, f"cx{j}") for j in range(2)]
+    cds = [synth.ct_draws(p, b.shape, seed, f"cx{j}") for j, b in enumerate(bits)]
+    dev = [api.encrypt_bits(p, s_dev, d(cd.mask), d(cd.noise), d(b)) for cd, b in zip(cds, bits)]
+    host = [orc.encrypt_bits(P, kd.s, cd.mask, cd.noise, b) for cd, b in zip(cds, bits)]
+    return (kind, w, 0, 0, dev[0], dev[1], host[0], host[1], (nb,))
+
+
+def test_cancel_queued_and_running(env):
+    """Cancelling requests.  A pool capped at 3,000 rows holds one 32-bit
+    multiplication (2,888 rows) and nothing beside it, so a 16-bit
+    multiplication and a gate submitted after it queue, in that order.  The
+    gate is cancelled while queued and the 32-bit multiplication while it
+    runs (it has 120 levels; the cancel comes within a few of them).
+    Neither output buffer is ever written, both report TFHE_ECANCELED, and
+    the running request's rows go back to the pool: the 16-bit
+    multiplication is admitted into them and completes, equal to the
+    oracle.  A finished, an already cancelled or an unknown request cannot
+    be cancelled."""
+    torch, api, p = env["torch"], env["api"], env["p"]
+    reqs = [_one_request(env, api.MUL, 32, 501), _one_request(env, api.MUL, 16, 502),
+            _one_request(env, api.GATE, api.AND, 503)]
+    sentinel = -12345
+    outs = [torch.full(req[8] + (api.LWE_STRIDE,), sentinel, dtype=torch.int32, device="cuda")
+            for req in reqs]
+    torch.cuda.synchronize()
+    ctx = api.Context(p)
+    ctx.set_keys(env["bk"], env["ksk"])
+    try:
+        ctx.serve_start(3000 * api.LWE_STRIDE * 4)
+        ids = [ctx.serve_submit(r[0], r[1], r[4], r[5], o, r[2], r[3])
+               for r, o in zip(reqs, outs)]
+        ctx.serve_cancel(ids[2])                  # queued behind the 16-bit multiplication
+        deadline = time.time() + 10.0
+        while ctx.serve_stats()["in_flight"] == 0 and time.time() < deadline:
+            time.sleep(1e-4)
+        assert ctx.serve_stats()["in_flight"] == 1
+        ctx.serve_cancel(ids[0])                  # admitted and running
+        for k in (0, 2):
+            with pytest.raises(api.TFHEError) as err:
+                ctx.serve_wait(ids[k], 10000)
+            assert err.value.code == -7           # TFHE_ECANCELED
+            assert ctx.serve_poll(ids[k])[0] == -7
+        ctx.serve_wait(ids[1], 120000)
+        for rid in (ids[0], ids[1], 10 ** 9):     # cancelled, completed, unknown
+            with pytest.raises(api.TFHEError) as err:
+                ctx.serve_cancel(rid)
+            assert err.value.code == -1           # TFHE_EINVAL
+        st = ctx.serve_stats()
+        ctx.serve_stop()
+        torch.cuda.synchronize()
+        assert st["submitted"] == 3 and st["completed"] == 1 and st["cancelled"] == 2
+        assert st["failed"] == 0 and st["in_flight"] == 0 and st["queued"] == 0
+        for k in (0, 2):
+            assert bool((outs[k] == sentinel).all()), k
+        got = outs[1].cpu().numpy().view(np.uint32)[..., :p.n + 1]
+        assert np.array_equal(got, _oracle(env, reqs[1]))
+    finally:
+        ctx.close()
+
+
 @pytest.fixture(scope="module")
 def full_env(orc):
     """Full parameters (n = 500), keys from the master seed."""
