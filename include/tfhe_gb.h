@@ -390,7 +390,9 @@ typedef struct {
     uint64_t pool_cap_bytes; /* the most it may grow to (the caller's cap, or */
                              /* the device's memory)                         */
     uint64_t pool_grows;     /* times admission grew the pool                */
-    uint64_t admitted_busy;  /* requests admitted while others were running  */
+    uint64_t admitted_busy;  /* requests admitted while others were admitted  */
+                             /* and unfinished (earlier in the same admission */
+                             /* pass included) or an iteration was in flight */
     uint64_t cancelled;      /* requests cancelled before they completed      */
 } tfhe_serve_info;
 
