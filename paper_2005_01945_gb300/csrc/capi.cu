@@ -32,6 +32,7 @@ int fail(tfhe_ctx *ctx, int code, const char *fmt, ...)
         va_start(ap, fmt);
         vsnprintf(buf, sizeof(buf), fmt, ap);
         va_end(ap);
+        std::lock_guard<std::mutex> lock(ctx->err_mu);
         ctx->err = buf;
     }
     return code;
@@ -218,6 +219,7 @@ int tfhe_last_error(const tfhe_ctx *ctx, char *buf, size_t len)
 {
     if (!ctx || !buf || len == 0)
         return TFHE_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->err_mu);
     std::snprintf(buf, len, "%s", ctx->err.c_str());
     return TFHE_OK;
 }

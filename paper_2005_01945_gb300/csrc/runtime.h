@@ -1,5 +1,6 @@
 // runtime.h -- host-side context shared by the C-ABI translation units.
 #pragma once
+#include <mutex>
 #include <string>
 
 #include <nvtx3/nvToolsExt.h>
@@ -24,7 +25,8 @@ struct tfhe_ctx {
     size_t big_rows = 0;
     bool keys_loaded = false;
     tgb::DevKeys keys{};
-    std::string err;
+    std::string err;                 // last failure message (guarded by err_mu: the
+    mutable std::mutex err_mu;       // serving calls fail from several threads)
     uint64_t launches = 0;           // kernels issued (graph nodes count per replay)
     size_t test_free_hbm = 0;        // test hook: serving takes this as the free HBM
     tgb::CircuitCache *circuits = nullptr;
