@@ -3,7 +3,9 @@ and widths submitted while others run; every result is bit-identical to the
 same request run alone and to the oracle (n = 16 ring-size-1024 parameters
 so the oracle is quick, and a mix of every served kind at full parameters,
 n = 500), and a pool budget smaller than the mix forces requests to wait
-for rows without changing any result."""
+for rows without changing any result.  Cancelled requests (queued or
+running) never write their outputs and give their rows back to the
+pool."""
 import concurrent.futures as cf
 import threading
 import time
