@@ -314,9 +314,14 @@ def mul_karatsuba(P: Params, bk, ksk, w: int, A, B, nthreads: int = 0):
 
 
 def gate3(P: Params, bk, ksk, op: int, ca, cb, cc) -> np.ndarray:
+    """One 3-input gate per row: ca, cb, cc are [n+1] or [count][n+1]."""
     ca, cb, cc, bk, ksk = _u32(ca), _u32(cb), _u32(cc), _u32(bk), _u32(ksk)
+    if not (ca.shape == cb.shape == cc.shape and ca.shape[-1] == P.n + 1 and ca.ndim <= 2):
+        raise ValueError("gate3: ca, cb, cc must be matching [n+1] or [count][n+1] arrays")
     out = np.empty_like(ca)
-    lib().orc_gate3(ctypes.byref(P), _p(bk), _p(ksk), int(op), _p(ca), _p(cb), _p(cc), _p(out))
+    rows = (ca, cb, cc, out) if ca.ndim == 1 else None
+    for a, b, c, o in ([rows] if rows else zip(ca, cb, cc, out)):
+        lib().orc_gate3(ctypes.byref(P), _p(bk), _p(ksk), int(op), _p(a), _p(b), _p(c), _p(o))
     return out
 
 
